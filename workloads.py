@@ -1,0 +1,119 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module holds input generation only: no step of the QR method is computed
+here, so neither side of a parity check can inherit a mistake from the other
+through it.
+
+Every matrix is float64, column-major (Fortran order), drawn from
+``numpy.random.default_rng(seed)`` (PCG64).  The shapes and distributions follow
+the workloads of the QR method (tall-skinny TSQR panels, square and tall
+matrices with graded column scales); the paper itself measures no dataset, so
+these seeded draws are the whole input story.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def gaussian(m: int, n: int, seed: int) -> np.ndarray:
+    """m x n matrix, entries iid N(0,1), Fortran order.
+
+    Drawn row-major as (n, m) and transposed so that each column is one
+    contiguous run of the generator's stream.
+    """
+    rng = np.random.default_rng(seed)
+    return np.asfortranarray(rng.standard_normal((n, m)).T)
+
+
+def column_scales(n: int, decades: float = 6.0) -> np.ndarray:
+    """Scale 10**(-decades * j / n) for 0-based column j (graded columns)."""
+    j = np.arange(n, dtype=np.float64)
+    return 10.0 ** (-decades * j / max(n, 1))
+
+
+def graded(m: int, n: int, seed: int, decades: float = 6.0) -> np.ndarray:
+    """Gaussian m x n with column j scaled by 10**(-decades*j/n)."""
+    a = gaussian(m, n, seed)
+    a *= column_scales(n, decades)[None, :]
+    return a
+
+
+def vector(m: int, seed: int) -> np.ndarray:
+    """Right-hand side b, iid N(0,1)."""
+    return np.random.default_rng(seed).standard_normal(m)
+
+
+def upper_triangular(m: int, n: int, seed: int) -> np.ndarray:
+    """m x n with a random upper triangle in its top n rows and zeros elsewhere."""
+    a = gaussian(m, n, seed)
+    a[np.tril_indices(m, -1, n)] = 0.0
+    return np.asfortranarray(a)
+
+
+def random_reflector_product(m: int, n: int, seed: int) -> np.ndarray:
+    """m x n matrix with orthonormal columns: leading n columns of a product of
+    n random elementary reflectors I - 2 u u^T / (u^T u), applied to [I; 0].
+
+    Formed by plain reflector products (not a QR routine), so that an
+    orthogonal test input does not depend on any QR implementation.
+    """
+    rng = np.random.default_rng(seed)
+    q = np.zeros((m, n))
+    q[:n, :n] = np.eye(n)
+    for _ in range(n):
+        u = rng.standard_normal(m)
+        q -= np.outer(u, (2.0 / (u @ u)) * (u @ q))
+    return np.asfortranarray(q)
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One named workload: A (m x n) and an optional right-hand side b."""
+    name: str
+    m: int
+    n: int
+    seed: int
+    graded: bool
+    rhs_seed: int | None = None
+
+    def matrix(self) -> np.ndarray:
+        if self.graded:
+            return graded(self.m, self.n, self.seed)
+        return gaussian(self.m, self.n, self.seed)
+
+    def rhs(self) -> np.ndarray | None:
+        return None if self.rhs_seed is None else vector(self.m, self.rhs_seed)
+
+    @property
+    def flops(self) -> float:
+        """Algorithmic Householder QR flop count 2mn^2 - 2n^3/3."""
+        return qr_flops(self.m, self.n)
+
+
+def qr_flops(m: int, n: int) -> float:
+    return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+
+
+def qr_flops_partial(m: int, n: int, k: int) -> float:
+    """Flops credited to the first k of n Householder steps: the whole count
+    minus the count of the (m-k) x (n-k) problem that remains."""
+    return qr_flops(m, n) - qr_flops(m - k, n - k)
+
+
+# Named workloads: a 1024 x 128 Gaussian with a Gaussian right-hand side (the
+# small case an unblocked CPU QR finishes in well under a second), and the two
+# large graded shapes (tall 32768 x 2048 and square 8192 x 8192, columns
+# scaled by 10^(-6j/n)).
+SMALL_1024x128 = Workload("gaussian_1024x128", 1024, 128, seed=0, graded=False, rhs_seed=1)
+TALL_32768x2048 = Workload("graded_32768x2048", 32768, 2048, seed=2, graded=True)
+SQUARE_8192 = Workload("graded_8192x8192", 8192, 8192, seed=3, graded=True)
+
+WORKLOADS = {w.name: w for w in (SMALL_1024x128, TALL_32768x2048, SQUARE_8192)}
+
+
+def log_uniform_int(rng: np.random.Generator, lo: int, hi: int) -> int:
+    return int(math.floor(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
