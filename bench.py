@@ -1,0 +1,326 @@
+"""Benchmark: FP64 recursive Householder QR (QR-EG with TSQR base case) on
+one GB300, reported as TFLOP/s at the algorithmic count 2mn^2 - 2n^3/3.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--layout panel|full] [--impl gbqr|reference]
+
+A step is one full factorization of the workload's matrix (every step of the
+path: non-finite scan, TSQR base cases, update and T-assembly GEMMs, the
+right-looking top-level updates).  Each step first restores A from a pristine
+device copy (included in the step; it is < 0.1 % of it).  The inputs are
+larger than L2, so no flush is needed between steps.  Under torchrun every
+rank factors its own matrix (independent replicas, no collective on the data
+path); the reported value is the flops of all ranks over the slowest rank's
+time.
+
+--impl reference times the CPU oracle (unblocked Householder QR, one
+thread) on a bounded sample of the same workload: the first k Householder
+steps of the same matrix, credited with the flops of those k steps.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+FP64_NOMINAL_TFLOPS = 1.25          # GB300 FP64 (CUDA and tensor cores), nominal
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+# Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 FMA) x 2.070 GHz.
+FP64_FLOP_PER_CLK_PER_SM = 4.0
+FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs peak; LS solves/s, p99 ms: mixed vs FP64"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--workload", default=workloads.SQUARE_8192.name, choices=sorted(workloads.WORKLOADS))
+    p.add_argument("--layout", default="panel", choices=["panel", "full"])
+    p.add_argument("--impl", default="gbqr", choices=["gbqr", "reference"])
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cutoff", type=int, default=0)
+    p.add_argument("--panel", type=int, default=0)
+    p.add_argument("--leaf", type=int, default=0)
+    p.add_argument("--fanout", type=int, default=0)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names[1:], parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample(a: np.ndarray, budget_s: float):
+    """Times the oracle on the first k Householder steps of a, with k sized so
+    that the run takes about budget_s seconds; returns (tflops, k, seconds)."""
+    import oracle
+    orc = oracle.default()
+    m, n = a.shape
+    k0 = max(1, min(n, 2))
+    t0 = time.perf_counter()
+    orc.house_qr(a, nsteps=k0)
+    t1 = time.perf_counter() - t0
+    per_step = t1 / k0
+    k = int(max(1, min(n, budget_s / max(per_step, 1e-9))))
+    t0 = time.perf_counter()
+    orc.house_qr(a, nsteps=k)
+    dt = time.perf_counter() - t0
+    return workloads.qr_flops_partial(m, n, k) / dt / 1e12, k, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = workloads.WORKLOADS[args.workload]
+    a = w.matrix()
+    # each step: a bounded sample (first k Householder steps) of the workload
+    per_step_budget = max(0.5, min(4.0, 150.0 / max(1, args.steps + args.warmup)))
+    import oracle
+    orc = oracle.default()
+    t0 = time.perf_counter()
+    orc.house_qr(a, nsteps=2)
+    per = (time.perf_counter() - t0) / 2
+    k = int(max(1, min(w.n, per_step_budget / max(per, 1e-9))))
+    for _ in range(args.warmup):
+        orc.house_qr(a, nsteps=k)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        orc.house_qr(a, nsteps=k)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    flops = workloads.qr_flops_partial(w.m, w.n, k) * args.steps
+    value = flops / total / 1e12
+    sample = f"first {k} of {w.n} Householder steps of the {w.m}x{w.n} matrix per step, single thread"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gbqr(args):
+    import ctypes
+
+    import torch
+
+    import paper_1805_05278_gb300 as gb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+
+    gb.build()
+    w = workloads.WORKLOADS[args.workload]
+    layout = gb.GBQR_T_PANEL if args.layout == "panel" else gb.GBQR_T_FULL
+    o = gb.opts(cutoff_b=args.cutoff, panel_nb=args.panel, leaf_rows=args.leaf, fanout=args.fanout)
+    nb = args.panel or gb.default_panel_nb(w.m, w.n)
+    trows = w.n if layout == gb.GBQR_T_FULL else min(nb, w.n)
+
+    a_host = workloads.graded(w.m, w.n, w.seed + rank) if w.graded else workloads.gaussian(w.m, w.n, w.seed + rank)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gb.Context(dev, stream)
+    A0 = gb.to_colmajor(a_host, f"cuda:{dev}")
+    A = gb.colmajor(w.m, w.n, f"cuda:{dev}")
+    T = gb.colmajor(trows, w.n, f"cuda:{dev}")
+    ws = torch.empty(gb.workspace_bytes(w.m, w.n, layout, o), dtype=torch.uint8, device=f"cuda:{dev}")
+    ctx.set_workspace(ws)
+
+    def step():
+        A.copy_(A0)
+        ctx.factor(A, T, layout, o)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    torch.cuda.synchronize()
+    st, _ = ctx.sync()
+    if st != gb.GBQR_OK:
+        raise RuntimeError(f"warm-up reported status {st}")
+
+    # timed region: K steps with launch tracing on, clocks sampled alongside
+    ctx.trace(True)
+    ctx.trace_read()
+    launches0 = ctx.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    trace = ctx.trace_read()
+    ctx.trace(False)
+    launches = ctx.launch_count() - launches0
+    clocks = clk.summary()
+    ms_step = ms_total / args.steps
+    if dist:
+        t = torch.tensor([ms_step], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = w.flops * world / (ms_step * 1e-3) / 1e12
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    a_pin = torch.from_numpy(np.ascontiguousarray(a_host.T)).pin_memory()   # (n, m) row-major = A column-major
+    t_pin = torch.empty((w.n, trows), dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for i in range(max(args.e2e_steps, 1) + 1):
+        a_pin.copy_(torch.from_numpy(np.ascontiguousarray(a_host.T)))
+        t0 = time.perf_counter()
+        gb.check(gb.gbqr_factor(ctx.handle, w.m, w.n, ctypes.c_void_p(a_pin.data_ptr()), w.m,
+                                ctypes.c_void_p(t_pin.data_ptr()), trows, layout, ctypes.byref(o)), "gbqr_factor(host)")
+        dt = time.perf_counter() - t0
+        if i > 0:
+            e2e_times.append(dt)
+    e2e_s = statistics.median(e2e_times)
+    e2e_value = w.flops * world / e2e_s / 1e12
+
+    # check the step's output against properties (cheap sampled parity lives in the tests)
+    st, info = ctx.sync()
+
+    gemm = trace.get("gemm", {})
+    achieved = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm.get("ms") else None
+    roofline = {
+        "bound": "alu", "kernel": "dgemm_kernel (update / T-assembly products)",
+        "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
+        "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.070 GHz (nominal 1.25 TFLOP/s FP64)",
+        "traffic": None,
+        "launches": gemm.get("launches"), "share_of_step": (gemm.get("ms", 0.0) / ms_total) if ms_total else None,
+    }
+    fams = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else None} for k, v in trace.items()}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        tf, k, dt = oracle_sample(a_host, args.cpu_seconds)
+        cpu = {"value": tf, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {k} of {w.n} Householder steps of the same {w.m}x{w.n} matrix ({dt:.1f} s, single thread)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed,
+                       "t_layout": args.layout, "panel_nb": nb if layout == gb.GBQR_T_PANEL else None,
+                       "cutoff_b": args.cutoff or 32, "parallelism": f"replicas x{world}",
+                       "l2": "inputs (%.0f MB) larger than L2, no flush" % (w.m * w.n * 8 / 1e6),
+                       "step": "restore A from a device copy + gbqr_factor"},
+            "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": w.m * w.n * 8,
+                    "d2h_bytes_per_step": w.m * w.n * 8 + trows * w.n * 8,
+                    "how": "gbqr_factor on pinned host buffers (H2D, factor, D2H inside the call)"},
+            "gpu_launches": launches,
+            "roofline": roofline,
+            "families": fams,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+            "status_after": int(st),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gbqr(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * gbqr.h - C ABI of a GB300 (sm_103a) library for recursive Householder QR
+ * and least squares, after Ballard, Demmel, Grigori, Jacquelin, Knight,
+ * "A 3D Parallel Algorithm for QR Decomposition" (arXiv 1805.05278).
+ *
+ * Method: the Elmroth-Gustavson recursion QR-EG (Algorithm 2, Section 2.4)
+ * in Householder (compact-WY) representation (Section 2.3), whose base case
+ * is TSQR over row blocks (Section 5, Appendix C) - the paper's 1D-CAQR-EG
+ * (Section 6) restated for the SMs of one GPU.
+ *
+ * Conventions shared by every call:
+ *   - Real FP64, column-major: element (i, j) of a matrix X with leading
+ *     dimension ldx is X[i + j*ldx].  m >= n >= 0 (Section 2.1).
+ *   - Matrix pointers are device pointers unless a call says otherwise.  The
+ *     caller owns every matrix; the library only borrows the pointers for the
+ *     duration of the stream-ordered work it enqueues.
+ *   - Calls are asynchronous on the context's stream.  A returned status
+ *     reports argument errors and launch failures; device-side conditions
+ *     (non-finite input) are collected in a device-side record that
+ *     gbqr_sync() reads.
+ *   - A context is not thread-safe: one host thread at a time per context.
+ *   - Every int64_t size must be >= 0; leading dimensions must be >= max(1, rows).
+ *
+ * Householder representation returned by gbqr_factor (Section 2.3):
+ *   Q = I - V T V^T, V unit lower trapezoidal (m x n, unit diagonal implied),
+ *   T upper triangular, R upper triangular (n x n).  V's strict lower
+ *   trapezoid and R's upper triangle overwrite A in place.  Reflector j is
+ *   H_j = I - tau_j v_j v_j^T with beta_j = -sgn(alpha_j) ||column||,
+ *   sgn(0) = +1 and no exception for an already-reduced column (tau_j = 2
+ *   there) - the convention that the TSQR reconstruction of Appendix C.2
+ *   produces, so that V, T and R are identical (up to rounding) to those of
+ *   unblocked Householder QR.
+ */
+#ifndef GBQR_H
+#define GBQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define GBQR_API __attribute__((visibility("default")))
+#else
+#define GBQR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbqr_ctx gbqr_ctx;
+
+typedef enum {
+    GBQR_OK = 0,
+    GBQR_EINVAL = 1,       /* invalid argument (size, leading dimension, null pointer) */
+    GBQR_ENOMEM = 2,       /* workspace too small or device allocation failed */
+    GBQR_ECUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    GBQR_ETIMEOUT = 4,     /* a bounded device-side wait ran out */
+    GBQR_ENONFINITE = 5,   /* input held NaN or Inf (reported by gbqr_sync) */
+    GBQR_ERANKDEF = 6,     /* least squares: R has an exactly zero diagonal entry */
+    GBQR_EBUSY = 7,        /* context busy (e.g. workspace in use by queued work) */
+    GBQR_EUNSUPPORTED = 8  /* valid request outside what this build implements */
+} gbqr_status;
+
+/* Storage of the kernel T. */
+typedef enum {
+    /* n x n upper triangular T of the whole Q = I - V T V^T, as returned by
+     * Algorithm 2 (pure QR-EG recursion, T assembled at every level). */
+    GBQR_T_FULL = 0,
+    /* nb x n: the n/nb diagonal blocks of T, block k (width w_k = min(nb,
+     * n - k*nb)) at T[0:w_k, k*nb : k*nb + w_k].  Produced by a right-looking
+     * top level over panels of width nb, each panel factored by QR-EG, so
+     * the superdiagonal blocks of T are never formed (Section 8.4).
+     * Q = Q_0 Q_1 ... with Q_k = I - V_k T_k V_k^T. */
+    GBQR_T_PANEL = 1
+} gbqr_t_layout;
+
+typedef enum {
+    GBQR_FP64 = 0,          /* every step in FP64 */
+    GBQR_MIXED_BF16 = 1,    /* reserved: tensor-core update GEMMs + refinement */
+    GBQR_MIXED_SPLITBF16 = 2,
+    GBQR_FP32 = 3
+} gbqr_prec;
+
+/* Algorithm parameters.  Zero selects the library's tuned default. */
+typedef struct {
+    int32_t cutoff_b;   /* QR-EG base-case threshold b: base case when n <= b
+                           (Algorithm 2); 1 <= b <= 64 */
+    int32_t panel_nb;   /* GBQR_T_PANEL: top-level panel width nb (>= 1) */
+    int32_t leaf_rows;  /* TSQR leaf height target m_p (>= b; Section 5 needs m_p >= n) */
+    int32_t fanout;     /* TSQR reduction-tree fan-out k (2..8; the paper's
+                           binomial tree is k = 2, Appendix C.1) */
+    int32_t reserved[4];
+} gbqr_opts;
+
+/* Device-side record of one or more calls since the last gbqr_sync(). */
+typedef struct {
+    int64_t nonfinite;     /* non-zero if a NaN/Inf input was seen */
+    int64_t zero_pivots;   /* reflectors whose column was exactly zero */
+    int64_t rankdef_col;   /* least squares: first j with R(j,j) == 0, else -1 */
+    int64_t reserved[5];
+} gbqr_info;
+
+/* Per-kernel-family totals of traced launches (see gbqr_trace_enable). */
+typedef struct {
+    char name[24];         /* "gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other" */
+    int64_t launches;
+    double ms;             /* summed device time between launch-bracketing events */
+    double flops;          /* summed algorithmic FP64 flops of those launches */
+    double bytes;          /* summed algorithmic bytes (operands read + written once) */
+} gbqr_trace_rec;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, enqueueing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Allocates nothing on the device until a call needs workspace.
+ * Errors: EINVAL (out NULL, bad device), ECUDA. */
+GBQR_API gbqr_status gbqr_create(gbqr_ctx **out, int device, void *cuda_stream);
+
+/* Synchronise the context's stream and release everything it owns. */
+GBQR_API gbqr_status gbqr_destroy(gbqr_ctx *ctx);
+
+/* Re-bind the context to another stream (work already queued stays where it is). */
+GBQR_API gbqr_status gbqr_set_stream(gbqr_ctx *ctx, void *cuda_stream);
+
+/* Caller-owned device workspace of `bytes` bytes (16-byte aligned), used
+ * instead of library allocations.  It must stay valid until the work using
+ * it completes.  ptr NULL returns to library-owned workspace (grown on demand
+ * by cudaMalloc, outside any stream capture). */
+GBQR_API gbqr_status gbqr_set_workspace(gbqr_ctx *ctx, void *ptr, size_t bytes);
+
+/* Workspace bytes that gbqr_factor / gbqr_apply_* / gbqr_form_q /
+ * gbqr_ls_solve need for an m x n problem with the given layout and options
+ * (opts NULL = defaults).  Returns 0 for invalid sizes. */
+GBQR_API size_t gbqr_workspace_bytes(int64_t m, int64_t n, int t_layout, const gbqr_opts *opts);
+
+/* Wait for the context's stream, then copy out (and clear) the device-side
+ * info record.  info may be NULL.  Returns ENONFINITE if non-finite input
+ * was seen, else OK (or ECUDA for an asynchronous CUDA error). */
+GBQR_API gbqr_status gbqr_sync(gbqr_ctx *ctx, gbqr_info *info);
+
+/* ---- factorization (Algorithm 2 with TSQR base case) -------------------- */
+
+/* QR-factor the m x n matrix A (m >= n) in place.
+ *   A   (m x n, lda):  in: A.  out: V's strict lower trapezoid and R's upper
+ *                      triangle (Householder representation, Section 2.3).
+ *   T   (ldt x n):     out: the kernel T in `t_layout` (GBQR_T_FULL: n x n,
+ *                      ldt >= n, zeros written below the diagonal;
+ *                      GBQR_T_PANEL: nb x n, ldt >= nb, nb = opts->panel_nb or
+ *                      the default that gbqr_default_panel_nb reports).
+ * Inductive case: n1 = floor(n/2); M1 = V_L^T A_R; M2 = T_L^T M1;
+ * A_R -= V_L M2; recursion on the trailing block; T12 = -T_L (V_L^T [0; V_R]) T_R
+ * (Algorithm 2).  Base case (n <= b): TSQR with leaf QR per CTA, a fan-out-k
+ * tree of structured R merges, the downsweep that forms the leading columns
+ * W of Q, and the Householder reconstruction X + S = LU, T = U S L^{-T},
+ * R = -S R_tree, V = W U^{-1} (Appendix C).
+ * A and T may instead both be HOST pointers (pageable or pinned): the call
+ * then stages them through device workspace, copies the results back and
+ * returns after the stream has synchronised.
+ * Errors: EINVAL (m < n, lda < m, ldt too small, bad opts), ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_factor(gbqr_ctx *ctx, int64_t m, int64_t n, double *A, int64_t lda,
+                        double *T, int64_t ldt, int t_layout, const gbqr_opts *opts);
+
+/* Default top-level panel width for GBQR_T_PANEL on an m x n problem. */
+GBQR_API int64_t gbqr_default_panel_nb(int64_t m, int64_t n);
+
+/* ---- applying Q (basis-kernel update equation, Section 2.3) ------------ */
+
+/* B <- Q^T B for the m x nrhs matrix B, with Q = I - V T V^T given by the
+ * packed V\R (from gbqr_factor, lda) and T in `t_layout` (nb = panel width
+ * for GBQR_T_PANEL, ignored for GBQR_T_FULL).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_apply_qt(gbqr_ctx *ctx, int64_t m, int64_t n, const double *VR, int64_t lda,
+                          const double *T, int64_t ldt, int t_layout, int64_t nb,
+                          int64_t nrhs, double *B, int64_t ldb);
+
+/* B <- Q B (same arguments as gbqr_apply_qt). */
+GBQR_API gbqr_status gbqr_apply_q(gbqr_ctx *ctx, int64_t m, int64_t n, const double *VR, int64_t lda,
+                         const double *T, int64_t ldt, int t_layout, int64_t nb,
+                         int64_t nrhs, double *B, int64_t ldb);
+
+/* Thin Q: Q (m x n, ldq) <- Q [I_n; 0].  Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_form_q(gbqr_ctx *ctx, int64_t m, int64_t n, const double *VR, int64_t lda,
+                        const double *T, int64_t ldt, int t_layout, int64_t nb,
+                        double *Q, int64_t ldq);
+
+/* ---- least squares (Section 2.1 problem, solved through the QR) -------- */
+
+/* x = argmin ||A x - b||_2 for m x n A of full column rank (m >= n):
+ * factor a workspace copy of A (A itself is not modified), c = Q^T b,
+ * x = R^{-1} c(0:n) by blocked back substitution.  b has m entries, x
+ * receives n.  prec must be GBQR_FP64 in this build (others: EUNSUPPORTED).
+ * info (may be NULL) receives rankdef_col after an internal synchronisation;
+ * an exactly zero R(j,j) gives ERANKDEF.  Synchronous: returns after x is
+ * written.  Errors: EINVAL, ENOMEM, ECUDA, ERANKDEF, EUNSUPPORTED. */
+GBQR_API gbqr_status gbqr_ls_solve(gbqr_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
+                          const double *b, double *x, int prec, gbqr_info *info);
+
+/* ---- tracing ------------------------------------------------------------ */
+
+/* Turn launch tracing on (non-zero) or off.  While on, every kernel launch is
+ * bracketed by CUDA events on the context's stream and its algorithmic
+ * flops/bytes are counted. */
+GBQR_API gbqr_status gbqr_trace_enable(gbqr_ctx *ctx, int on);
+
+/* Synchronise, then write up to `max` per-family totals to out[] and their
+ * number to *count; clears the trace. */
+GBQR_API gbqr_status gbqr_trace_read(gbqr_ctx *ctx, gbqr_trace_rec *out, int max, int *count);
+
+/* Number of kernel launches the context has issued since creation. */
+GBQR_API int64_t gbqr_launch_count(const gbqr_ctx *ctx);
+
+/* ---- diagnostics -------------------------------------------------------- */
+
+/* Measure the FP64 FMA throughput of CUDA device `device`: kind 0 = DFMA on
+ * the CUDA cores, kind 1 = DMMA (mma.sync m8n8k4 f64 on the tensor cores).
+ * Runs `iters` iterations of 8 independent chains per thread on 8 CTAs of
+ * 256 threads per SM, best of 3 timed launches; *tflops receives TFLOP/s.
+ * The paper has no counterpart: this is the denominator of the roofline
+ * that the FP64 kernels are reported against.  Synchronous; allocates 8
+ * bytes.  Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_fp64_peak(int device, int kind, int iters, double *tflops);
+
+/* Human-readable name of a status. */
+GBQR_API const char *gbqr_strerror(gbqr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBQR_H */

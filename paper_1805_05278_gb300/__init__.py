@@ -1,0 +1,272 @@
+"""Python binding of libgbqr (include/gbqr.h): recursive Householder QR
+(QR-EG with a TSQR base case) and least squares on one GB300.
+
+Argument marshalling only.  The module-level ``gbqr_*`` functions mirror the
+C ABI one to one (same names, raw pointers and sizes); ``Context`` wraps them
+for torch tensors, passing ``data_ptr()`` and the current CUDA stream.  Every
+step of the computation runs in the library's CUDA kernels.  If the library is
+not built, ``load()`` raises: there is no fallback path.
+
+Matrices are column-major float64.  A torch tensor ``X`` of shape (m, n) is
+accepted when ``X.stride(0) == 1`` (a Fortran-ordered view, e.g. the ``.T`` of
+a contiguous (n, m) tensor); its leading dimension is ``X.stride(1)``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libgbqr.so")
+
+# status codes (gbqr_status)
+GBQR_OK, GBQR_EINVAL, GBQR_ENOMEM, GBQR_ECUDA, GBQR_ETIMEOUT = 0, 1, 2, 3, 4
+GBQR_ENONFINITE, GBQR_ERANKDEF, GBQR_EBUSY, GBQR_EUNSUPPORTED = 5, 6, 7, 8
+# T layouts (gbqr_t_layout) and precisions (gbqr_prec)
+GBQR_T_FULL, GBQR_T_PANEL = 0, 1
+GBQR_FP64, GBQR_MIXED_BF16, GBQR_MIXED_SPLITBF16, GBQR_FP32 = 0, 1, 2, 3
+
+_I64 = ctypes.c_int64
+_P = ctypes.c_void_p
+
+
+class gbqr_opts(ctypes.Structure):
+    _fields_ = [("cutoff_b", ctypes.c_int32), ("panel_nb", ctypes.c_int32),
+                ("leaf_rows", ctypes.c_int32), ("fanout", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+class gbqr_info(ctypes.Structure):
+    _fields_ = [("nonfinite", ctypes.c_int64), ("zero_pivots", ctypes.c_int64),
+                ("rankdef_col", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+
+
+class gbqr_trace_rec(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+# name -> (restype, argtypes): the declarations of include/gbqr.h
+SIGNATURES = {
+    "gbqr_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _P]),
+    "gbqr_destroy": (ctypes.c_int, [_P]),
+    "gbqr_set_stream": (ctypes.c_int, [_P, _P]),
+    "gbqr_set_workspace": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "gbqr_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, ctypes.c_int, ctypes.POINTER(gbqr_opts)]),
+    "gbqr_sync": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_info)]),
+    "gbqr_factor": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.POINTER(gbqr_opts)]),
+    "gbqr_default_panel_nb": (_I64, [_I64, _I64]),
+    "gbqr_apply_qt": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _I64, _P, _I64]),
+    "gbqr_apply_q": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _I64, _P, _I64]),
+    "gbqr_form_q": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _P, _I64]),
+    "gbqr_ls_solve": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _P, ctypes.c_int, ctypes.POINTER(gbqr_info)]),
+    "gbqr_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "gbqr_trace_read": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_trace_rec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "gbqr_launch_count": (_I64, [_P]),
+    "gbqr_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gbqr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (nvcc); returns its path."""
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def load(path: str | None = None):
+    """Load libgbqr.so and bind every C ABI function into this module."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libgbqr.so is not built ({p}); run paper_1805_05278_gb300.build()")
+        lib = ctypes.CDLL(p)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+            globals()[name] = f
+        _lib = lib
+        return lib
+
+
+class GbqrError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        load()
+        msg = gbqr_strerror(status).decode()  # noqa: F821 (bound by load)
+        super().__init__(f"{what}: {msg} (status {status})")
+        self.status = status
+
+
+def check(status: int, what: str) -> int:
+    if status != GBQR_OK:
+        raise GbqrError(status, what)
+    return status
+
+
+def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int = 0) -> gbqr_opts:
+    o = gbqr_opts()
+    o.cutoff_b, o.panel_nb, o.leaf_rows, o.fanout = cutoff_b, panel_nb, leaf_rows, fanout
+    return o
+
+
+def _cm(x, name: str):
+    """(pointer, rows, cols, leading dimension) of a column-major float64 tensor."""
+    import torch
+    if x.dtype != torch.float64:
+        raise TypeError(f"{name} must be float64")
+    if x.dim() == 1:
+        return x.data_ptr(), x.shape[0], 1, max(1, x.shape[0])
+    if x.dim() != 2 or (x.stride(0) != 1 and x.shape[0] > 1):
+        raise ValueError(f"{name} must be a column-major 2-D tensor (stride(0) == 1)")
+    return x.data_ptr(), x.shape[0], x.shape[1], max(1, x.stride(1), x.shape[0] if x.shape[1] == 1 else 1)
+
+
+def colmajor(m: int, n: int, device="cuda", fill=None):
+    """A new column-major m x n float64 tensor (optionally filled)."""
+    import torch
+    t = torch.empty((n, m), dtype=torch.float64, device=device).T
+    if fill is not None:
+        t.fill_(fill)
+    return t
+
+
+def to_colmajor(a, device="cuda", pin: bool = False):
+    """Column-major float64 tensor holding the numpy array a (m x n or m)."""
+    import numpy as np
+    import torch
+    a = np.asarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        t = torch.from_numpy(a.copy())
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(a.T)).T
+    if device == "cpu":
+        return t.pin_memory() if pin else t
+    return t.to(device)
+
+
+def to_numpy(t):
+    """Fortran-ordered numpy copy of a column-major tensor."""
+    import numpy as np
+    x = t.detach().cpu()
+    return np.asfortranarray(x.numpy())
+
+
+class Context:
+    """A gbqr context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = _P()
+        check(gbqr_create(ctypes.byref(h), device, _P(stream.cuda_stream)), "gbqr_create")  # noqa: F821
+        self.handle = h
+        self._workspace = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gbqr_destroy(self.handle)  # noqa: F821
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- workspace / sync / tracing
+    def set_workspace(self, tensor):
+        """Hand the library a caller-owned workspace (any CUDA tensor)."""
+        self._workspace = tensor
+        if tensor is None:
+            return check(gbqr_set_workspace(self.handle, None, 0), "gbqr_set_workspace")  # noqa: F821
+        nbytes = tensor.numel() * tensor.element_size()
+        return check(gbqr_set_workspace(self.handle, _P(tensor.data_ptr()), nbytes), "gbqr_set_workspace")  # noqa: F821
+
+    def sync(self):
+        info = gbqr_info()
+        st = gbqr_sync(self.handle, ctypes.byref(info))  # noqa: F821
+        return st, info
+
+    def trace(self, on: bool = True):
+        check(gbqr_trace_enable(self.handle, 1 if on else 0), "gbqr_trace_enable")  # noqa: F821
+
+    def trace_read(self) -> dict:
+        recs = (gbqr_trace_rec * 8)()
+        cnt = ctypes.c_int(0)
+        check(gbqr_trace_read(self.handle, recs, 8, ctypes.byref(cnt)), "gbqr_trace_read")  # noqa: F821
+        return {r.name.decode(): {"launches": r.launches, "ms": r.ms, "flops": r.flops, "bytes": r.bytes}
+                for r in recs[:cnt.value]}
+
+    def launch_count(self) -> int:
+        return int(gbqr_launch_count(self.handle))  # noqa: F821
+
+    # ---- computation
+    def factor(self, A, T, layout: int = GBQR_T_PANEL, o: gbqr_opts | None = None) -> int:
+        """In-place QR of A (column-major m x n); T receives the kernel."""
+        pa, m, n, lda = _cm(A, "A")
+        pt, _, _, ldt = _cm(T, "T")
+        return check(gbqr_factor(self.handle, m, n, _P(pa), lda, _P(pt), ldt, layout,  # noqa: F821
+                                 ctypes.byref(o) if o is not None else None), "gbqr_factor")
+
+    def _apply(self, fn, VR, T, layout, nb, B):
+        pv, m, n, lda = _cm(VR, "VR")
+        pt, _, _, ldt = _cm(T, "T")
+        pb, mb, nrhs, ldb = _cm(B, "B")
+        return check(fn(self.handle, m, n, _P(pv), lda, _P(pt), ldt, layout, nb, nrhs, _P(pb), ldb), fn.__name__)
+
+    def apply_qt(self, VR, T, B, layout: int = GBQR_T_PANEL, nb: int = 0) -> int:
+        return self._apply(gbqr_apply_qt, VR, T, layout, nb, B)  # noqa: F821
+
+    def apply_q(self, VR, T, B, layout: int = GBQR_T_PANEL, nb: int = 0) -> int:
+        return self._apply(gbqr_apply_q, VR, T, layout, nb, B)  # noqa: F821
+
+    def form_q(self, VR, T, Q, layout: int = GBQR_T_PANEL, nb: int = 0) -> int:
+        pv, m, n, lda = _cm(VR, "VR")
+        pt, _, _, ldt = _cm(T, "T")
+        pq, _, _, ldq = _cm(Q, "Q")
+        return check(gbqr_form_q(self.handle, m, n, _P(pv), lda, _P(pt), ldt, layout, nb, _P(pq), ldq),  # noqa: F821
+                     "gbqr_form_q")
+
+    def ls_solve(self, A, b, x, prec: int = GBQR_FP64):
+        pa, m, n, lda = _cm(A, "A")
+        info = gbqr_info()
+        st = gbqr_ls_solve(self.handle, m, n, _P(pa), lda, _P(b.data_ptr()), _P(x.data_ptr()), prec,  # noqa: F821
+                           ctypes.byref(info))
+        return st, info
+
+
+def workspace_bytes(m: int, n: int, layout: int = GBQR_T_PANEL, o: gbqr_opts | None = None) -> int:
+    load()
+    return int(gbqr_workspace_bytes(m, n, layout, ctypes.byref(o) if o is not None else None))  # noqa: F821
+
+
+def fp64_peak(device: int = 0, kind: int = 0, iters: int = 20000) -> float:
+    """Measured FP64 TFLOP/s of the device (kind 0 = DFMA, 1 = DMMA)."""
+    load()
+    out = ctypes.c_double(0.0)
+    check(gbqr_fp64_peak(device, kind, iters, ctypes.byref(out)), "gbqr_fp64_peak")  # noqa: F821
+    return out.value
+
+
+def default_panel_nb(m: int, n: int) -> int:
+    load()
+    return int(gbqr_default_panel_nb(m, n))  # noqa: F821

@@ -1,0 +1,615 @@
+// C ABI of the library (include/gbqr.h) and the host-side drivers:
+//   - the QR-EG recursion of Algorithm 2 (GBQR_T_FULL),
+//   - a right-looking top level over panels of width nb whose panels are
+//     factored by QR-EG, never forming superdiagonal blocks of T
+//     (Section 8.4; GBQR_T_PANEL),
+//   - applying Q / Q^T and forming the thin Q (basis-kernel update,
+//     Section 2.3), and the least-squares solve built on them.
+// All device work is enqueued on the context's stream; nothing here computes
+// on the host.
+#include "common.cuh"
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using namespace gbqr;
+
+namespace {
+
+constexpr int kDefaultCutoff = 32;
+constexpr int kDefaultFanout = 2;
+constexpr int64_t kDefaultPanel = 128;
+
+struct DeviceInfo {
+    unsigned long long nonfinite;
+    long long rankdef;
+};
+
+// ------------------------------------------------------------ event tracer
+struct EventTracer final : Tracer {
+    struct Rec { Family f; size_t e0, e1; double flops, bytes; };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> recs;
+    size_t used = 0, open = 0;
+    bool failed = false;
+
+    size_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { failed = true; return SIZE_MAX; }
+            pool.push_back(e);
+        }
+        return used++;
+    }
+    void begin(cudaStream_t s, Family) override {
+        open = next();
+        if (open != SIZE_MAX) cudaEventRecord(pool[open], s);
+    }
+    void end(cudaStream_t s, Family f, double flops, double bytes) override {
+        size_t e = next();
+        if (e == SIZE_MAX || open == SIZE_MAX) return;
+        cudaEventRecord(pool[e], s);
+        recs.push_back({f, open, e, flops, bytes});
+    }
+    ~EventTracer() override {
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+const char *kFamilyNames[FAM_COUNT] = {"gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other"};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Params {
+    int b = kDefaultCutoff;
+    int64_t nb = kDefaultPanel;
+    int leaf_rows = 0;
+    int fanout = kDefaultFanout;
+};
+
+bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
+    Params r;
+    r.nb = gbqr_default_panel_nb(m, n);
+    if (o) {
+        if (o->cutoff_b < 0 || o->cutoff_b > kMaxPanel) return false;
+        if (o->panel_nb < 0 || o->leaf_rows < 0) return false;
+        if (o->fanout != 0 && (o->fanout < 2 || o->fanout > 8)) return false;
+        if (o->cutoff_b) r.b = o->cutoff_b;
+        if (o->panel_nb) r.nb = o->panel_nb;
+        if (o->leaf_rows) r.leaf_rows = o->leaf_rows;
+        if (o->fanout) r.fanout = o->fanout;
+    }
+    r.nb = std::max<int64_t>(1, r.nb);
+    *p = r;
+    return true;
+}
+
+// Workspace regions (bytes, 256-aligned) for an m x n problem.
+struct Layout {
+    size_t partial = 0, gcount = 0, tR = 0, tT = 0, tY = 0, tX = 0, tcount = 0;
+    size_t M1 = 0, M2 = 0, bigA = 0, bigT = 0, vec = 0;
+    size_t total = 0;
+    size_t n_partial = 0, n_gcount = 0, n_M = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
+    TsqrPlan tsqr;
+};
+
+Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num_sms) {
+    Layout L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 16), 256); return o; };
+    L.n_partial = gemm_partial_elems_max(num_sms);
+    L.n_gcount = gemm_counters_max(num_sms);
+    const int w = (int)std::max<int64_t>(1, std::min<int64_t>(pr.b, n));
+    L.tsqr = tsqr_plan_bound(std::max<int64_t>(m, 1), w, pr.leaf_rows, pr.fanout, num_sms);
+    const int64_t nb = std::min<int64_t>(pr.nb, std::max<int64_t>(n, 1));
+    // temporaries of the update / T-assembly products and of applying Q
+    size_t nM = (size_t)((n + 1) / 2) * (size_t)(n / 2 + 1);
+    nM = std::max(nM, (size_t)nb * (size_t)std::max<int64_t>(n, 1));
+    if (t_layout == GBQR_T_FULL) nM = std::max(nM, (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1));
+    L.n_M = nM;
+    L.n_bigA = (size_t)std::max<int64_t>(m, 1) * (size_t)std::max<int64_t>(n, 1);
+    L.n_bigT = (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1);
+    L.partial = take(L.n_partial * 8);
+    L.counter_bytes = align_up(L.n_gcount * 4, 16) + L.tsqr.ncount * 4;
+    L.gcount = take(L.counter_bytes);
+    L.tcount = L.gcount + align_up(L.n_gcount * 4, 16);
+    L.tR = take(L.tsqr.nR * 8);
+    L.tT = take(L.tsqr.nT * 8);
+    L.tY = take(L.tsqr.nY * 8);
+    L.tX = take(L.tsqr.nX * 8);
+    L.M1 = take(nM * 8);
+    L.M2 = take(nM * 8);
+    L.bigA = take(L.n_bigA * 8);
+    L.bigT = take(L.n_bigT * 8);
+    L.vec = take((size_t)std::max<int64_t>(m, 1) * 8);
+    L.total = off;
+    return L;
+}
+
+}  // namespace
+
+struct gbqr_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 152;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = true;
+    DeviceInfo *dinfo = nullptr;
+    int64_t launches = 0;
+    EventTracer *tracer = nullptr;
+    bool tracing = false;
+
+    Exec exec() {
+        Exec e;
+        e.stream = stream;
+        e.tracer = tracing ? tracer : nullptr;
+        e.launches = &launches;
+        e.num_sms = num_sms;
+        e.device = device;
+        return e;
+    }
+};
+
+namespace {
+
+// Per-call view of the carved workspace.
+struct Work {
+    gbqr_ctx *cx;
+    Exec ex;
+    Layout L;
+    Params pr;
+    GemmScratch gs;
+    TsqrWork tw;
+    double *M1, *M2, *bigA, *bigT, *vec;
+};
+
+gbqr_status ensure_workspace(gbqr_ctx *cx, size_t bytes) {
+    if (bytes <= cx->ws_bytes) return GBQR_OK;
+    if (!cx->ws_owned) return GBQR_ENOMEM;
+    if (cx->ws) {
+        cudaStreamSynchronize(cx->stream);
+        cudaFree(cx->ws);
+        cx->ws = nullptr;
+        cx->ws_bytes = 0;
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return GBQR_ENOMEM; }
+    cx->ws = (char *)p;
+    cx->ws_bytes = bytes;
+    return GBQR_OK;
+}
+
+gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const Params &pr, Work *w) {
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    w->cx = cx;
+    w->pr = pr;
+    w->L = make_layout(m, n, t_layout, pr, cx->num_sms);
+    gbqr_status st = ensure_workspace(cx, w->L.total);
+    if (st != GBQR_OK) return st;
+    w->ex = cx->exec();
+    char *base = cx->ws;
+    w->gs.partial = (double *)(base + w->L.partial);
+    w->gs.partial_elems = w->L.n_partial;
+    w->gs.counters = (unsigned *)(base + w->L.gcount);
+    w->gs.ncounters = w->L.n_gcount;
+    w->tw.R = (double *)(base + w->L.tR);
+    w->tw.T = (double *)(base + w->L.tT);
+    w->tw.Y = (double *)(base + w->L.tY);
+    w->tw.X = (double *)(base + w->L.tX);
+    w->tw.counters = (unsigned *)(base + w->L.tcount);
+    w->M1 = (double *)(base + w->L.M1);
+    w->M2 = (double *)(base + w->L.M2);
+    w->bigA = (double *)(base + w->L.bigA);
+    w->bigT = (double *)(base + w->L.bigT);
+    w->vec = (double *)(base + w->L.vec);
+    // arrival counters start at zero (every kernel leaves them zero again)
+    if (cudaMemsetAsync(base + w->L.gcount, 0, w->L.counter_bytes, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    return GBQR_OK;
+}
+
+#define TRY(x) do { gbqr_status _s = (x); if (_s != GBQR_OK) return _s; } while (0)
+
+// C (mr x nc) <- (I - V op(T) V^T) C; op(T) = T^T when trans.  V is the unit
+// lower trapezoidal mr x kv basis, T the kv x kv upper triangular kernel.
+gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
+                        const double *V, int64_t ldv, const double *T, int64_t ldt, double *C, int64_t ldc) {
+    if (mr <= 0 || nc <= 0 || kv <= 0) return GBQR_OK;
+    if ((size_t)kv * (size_t)nc > w.L.n_M) return GBQR_ENOMEM;
+    GemmOp g;
+    g.M = kv; g.N = nc; g.K = mr;
+    g.A = V; g.lda = ldv; g.ta = true; g.maskA = MASK_UNIT_LOWER;
+    g.B = C; g.ldb = ldc; g.C = w.M1; g.ldc = kv;
+    TRY(gemm(w.ex, g, w.gs));
+    GemmOp h;
+    h.M = kv; h.N = nc; h.K = kv;
+    h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
+    h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
+    TRY(gemm(w.ex, h, w.gs));
+    GemmOp u;
+    u.M = mr; u.N = nc; u.K = kv;
+    u.A = V; u.lda = ldv; u.ta = false; u.maskA = MASK_UNIT_LOWER;
+    u.B = w.M2; u.ldb = kv; u.C = C; u.ldc = ldc; u.alpha = -1.0; u.beta = 1.0;
+    return gemm(w.ex, u, w.gs);
+}
+
+// Base case: TSQR of the m x n panel (n <= b).
+gbqr_status base_qr(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt) {
+    TsqrPlan pl;
+    if (!tsqr_plan(m, (int)n, w.pr.leaf_rows, w.pr.fanout, w.ex.num_sms, &pl)) return GBQR_EINVAL;
+    if (pl.nR > w.L.tsqr.nR || pl.nT > w.L.tsqr.nT || pl.nY > w.L.tsqr.nY || pl.ncount > w.L.tsqr.ncount)
+        return GBQR_ENOMEM;
+    return tsqr_run(w.ex, pl, A, lda, T, ldt, w.tw);
+}
+
+// Algorithm 2: (V, T, R) = QR-EG(A, b), V\R in place over A, T (n x n) at T.
+gbqr_status qr_eg(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt) {
+    if (n <= 0) return GBQR_OK;
+    if (n <= w.pr.b) return base_qr(w, m, n, A, lda, T, ldt);
+    const int64_t n1 = n / 2, n2 = n - n1;
+    double *AR = A + n1 * lda;
+    TRY(qr_eg(w, m, n1, A, lda, T, ldt));                  // left recursion
+    // M1 = V_L^T A_R ; M2 = T_L^T M1 ; A_R -= V_L M2
+    TRY(apply_block(w, true, m, n2, n1, A, lda, T, ldt, AR, lda));
+    // right recursion on B22
+    double *TR = T + n1 + n1 * ldt;
+    TRY(qr_eg(w, m - n1, n2, A + n1 + n1 * lda, lda, TR, ldt));
+    // M3 = V_L(n1:m, :)^T V_R ; M4 = M3 T_R ; T12 = -T_L M4
+    if ((size_t)n1 * (size_t)n2 > w.L.n_M) return GBQR_ENOMEM;
+    GemmOp g3;
+    g3.M = n1; g3.N = n2; g3.K = m - n1;
+    g3.A = A + n1; g3.lda = lda; g3.ta = true; g3.maskA = MASK_NONE;
+    g3.B = A + n1 + n1 * lda; g3.ldb = lda; g3.maskB = MASK_UNIT_LOWER;
+    g3.C = w.M1; g3.ldc = n1;
+    TRY(gemm(w.ex, g3, w.gs));
+    GemmOp g4;
+    g4.M = n1; g4.N = n2; g4.K = n2;
+    g4.A = w.M1; g4.lda = n1; g4.ta = false;
+    g4.B = TR; g4.ldb = ldt; g4.maskB = MASK_UPPER;
+    g4.C = w.M2; g4.ldc = n1;
+    TRY(gemm(w.ex, g4, w.gs));
+    GemmOp g5;
+    g5.M = n1; g5.N = n2; g5.K = n1;
+    g5.A = T; g5.lda = ldt; g5.ta = false; g5.maskA = MASK_UPPER;
+    g5.B = w.M2; g5.ldb = n1;
+    g5.C = T + n1 * ldt; g5.ldc = ldt; g5.alpha = -1.0; g5.beta = 0.0;
+    return gemm(w.ex, g5, w.gs);
+}
+
+// Zero T(i, j) for i > (j mod nb) (the strict lower part of every block).
+__global__ void zero_below_blocks_kernel(int64_t rows, int64_t n, int64_t nb, double *T, int64_t ldt) {
+    const int64_t total = rows * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e % rows, j = e / rows;
+        if (i > j % nb) T[i + j * ldt] = 0.0;
+    }
+}
+
+gbqr_status zero_below_blocks(Work &w, int64_t rows, int64_t n, int64_t nb, double *T, int64_t ldt) {
+    if (rows <= 1 || n <= 0) return GBQR_OK;
+    trace_begin(w.ex, FAM_OTHER);
+    const int64_t total = rows * n;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)w.ex.num_sms * 8));
+    zero_below_blocks_kernel<<<grid, 256, 0, w.ex.stream>>>(rows, n, nb, T, ldt);
+    return trace_end(w.ex, FAM_OTHER, 0.0, 4.0 * (double)total);
+}
+
+gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt, int layout) {
+    DeviceInfo *di = w.cx->dinfo;
+    TRY(scan_nonfinite(w.ex, m, n, A, lda, &di->nonfinite));
+    if (layout == GBQR_T_FULL) {
+        TRY(zero_below_blocks(w, n, n, std::max<int64_t>(n, 1), T, ldt));
+        return qr_eg(w, m, n, A, lda, T, ldt);
+    }
+    const int64_t nb = std::min<int64_t>(w.pr.nb, n);
+    TRY(zero_below_blocks(w, nb, n, nb, T, ldt));
+    for (int64_t j0 = 0; j0 < n; j0 += nb) {
+        const int64_t wd = std::min<int64_t>(nb, n - j0);
+        double *Ap = A + j0 + j0 * lda;
+        double *Tk = T + j0 * ldt;
+        TRY(qr_eg(w, m - j0, wd, Ap, lda, Tk, ldt));
+        if (j0 + wd < n)
+            TRY(apply_block(w, true, m - j0, n - j0 - wd, wd, Ap, lda, Tk, ldt, A + j0 + (j0 + wd) * lda, lda));
+    }
+    return GBQR_OK;
+}
+
+// B <- Q^T B (trans) or Q B, for either T layout.  col0 > 0 restricts the
+// update of panel k to columns >= its first column (used by form_q, where
+// the columns to the left are still unit vectors that Q_k leaves alone).
+gbqr_status apply_q_any(Work &w, bool trans, int64_t m, int64_t n, const double *VR, int64_t lda,
+                        const double *T, int64_t ldt, int layout, int64_t nb, int64_t nrhs,
+                        double *B, int64_t ldb, bool form_q_structure) {
+    if (n <= 0 || nrhs <= 0) return GBQR_OK;
+    if (layout == GBQR_T_FULL && !form_q_structure)
+        return apply_block(w, trans, m, nrhs, n, VR, lda, T, ldt, B, ldb);
+    // blocked over panels of width nb; for GBQR_T_FULL the panel kernels are
+    // the diagonal blocks of T (those of consecutive reflectors).
+    const int64_t pb = (layout == GBQR_T_FULL) ? std::min<int64_t>(kDefaultPanel, n) : nb;
+    const int64_t npan = (n + pb - 1) / pb;
+    for (int64_t q = 0; q < npan; ++q) {
+        const int64_t k = trans ? q : npan - 1 - q;
+        const int64_t j0 = k * pb, wd = std::min<int64_t>(pb, n - j0);
+        const double *Tk = (layout == GBQR_T_FULL) ? T + j0 + j0 * ldt : T + j0 * ldt;
+        const int64_t c0 = form_q_structure ? j0 : 0;
+        TRY(apply_block(w, trans, m - j0, nrhs - c0, wd, VR + j0 + j0 * lda, lda, Tk, ldt, B + j0 + c0 * ldb, ldb));
+    }
+    return GBQR_OK;
+}
+
+bool is_host_pointer(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return true; }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+gbqr_status check_layout_args(int64_t m, int64_t n, int64_t lda, int64_t ldt, int layout, int64_t nb) {
+    if (m < 0 || n < 0 || m < n) return GBQR_EINVAL;
+    if (lda < std::max<int64_t>(1, m)) return GBQR_EINVAL;
+    if (layout == GBQR_T_FULL) {
+        if (ldt < std::max<int64_t>(1, n)) return GBQR_EINVAL;
+    } else if (layout == GBQR_T_PANEL) {
+        if (nb < 1 || ldt < std::max<int64_t>(1, std::min(nb, n))) return GBQR_EINVAL;
+    } else {
+        return GBQR_EINVAL;
+    }
+    return GBQR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t gbqr_default_panel_nb(int64_t m, int64_t n) {
+    (void)m;
+    return std::max<int64_t>(1, std::min<int64_t>(kDefaultPanel, n));
+}
+
+const char *gbqr_strerror(gbqr_status s) {
+    switch (s) {
+        case GBQR_OK: return "ok";
+        case GBQR_EINVAL: return "invalid argument";
+        case GBQR_ENOMEM: return "out of workspace or device memory";
+        case GBQR_ECUDA: return "CUDA error";
+        case GBQR_ETIMEOUT: return "device-side wait timed out";
+        case GBQR_ENONFINITE: return "non-finite input";
+        case GBQR_ERANKDEF: return "rank deficient (zero diagonal in R)";
+        case GBQR_EBUSY: return "context busy";
+        case GBQR_EUNSUPPORTED: return "unsupported in this build";
+    }
+    return "unknown status";
+}
+
+gbqr_status gbqr_create(gbqr_ctx **out, int device, void *cuda_stream) {
+    if (!out) return GBQR_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) { cudaGetLastError(); return GBQR_ECUDA; }
+    if (device < 0 || device >= ndev) return GBQR_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return GBQR_ECUDA;
+    gbqr_ctx *cx = new (std::nothrow) gbqr_ctx();
+    if (!cx) return GBQR_ENOMEM;
+    cx->device = device;
+    cx->stream = (cudaStream_t)cuda_stream;
+    if (cudaDeviceGetAttribute(&cx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete cx;
+        return GBQR_ECUDA;
+    }
+    if (cudaMalloc((void **)&cx->dinfo, sizeof(DeviceInfo)) != cudaSuccess) { delete cx; return GBQR_ENOMEM; }
+    DeviceInfo zero{0ull, LLONG_MAX};
+    if (cudaMemcpy(cx->dinfo, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(cx->dinfo);
+        delete cx;
+        return GBQR_ECUDA;
+    }
+    cx->tracer = new (std::nothrow) EventTracer();
+    *out = cx;
+    return GBQR_OK;
+}
+
+gbqr_status gbqr_destroy(gbqr_ctx *cx) {
+    if (!cx) return GBQR_EINVAL;
+    cudaSetDevice(cx->device);
+    cudaStreamSynchronize(cx->stream);
+    if (cx->ws_owned && cx->ws) cudaFree(cx->ws);
+    if (cx->dinfo) cudaFree(cx->dinfo);
+    delete cx->tracer;
+    delete cx;
+    return GBQR_OK;
+}
+
+gbqr_status gbqr_set_stream(gbqr_ctx *cx, void *cuda_stream) {
+    if (!cx) return GBQR_EINVAL;
+    cx->stream = (cudaStream_t)cuda_stream;
+    return GBQR_OK;
+}
+
+gbqr_status gbqr_set_workspace(gbqr_ctx *cx, void *ptr, size_t bytes) {
+    if (!cx) return GBQR_EINVAL;
+    if (ptr && ((uintptr_t)ptr % 16) != 0) return GBQR_EINVAL;
+    if (cx->ws_owned && cx->ws) {
+        cudaStreamSynchronize(cx->stream);
+        cudaFree(cx->ws);
+    }
+    cx->ws = (char *)ptr;
+    cx->ws_bytes = ptr ? bytes : 0;
+    cx->ws_owned = (ptr == nullptr);
+    return GBQR_OK;
+}
+
+size_t gbqr_workspace_bytes(int64_t m, int64_t n, int t_layout, const gbqr_opts *opts) {
+    if (m < 0 || n < 0 || m < n) return 0;
+    if (t_layout != GBQR_T_FULL && t_layout != GBQR_T_PANEL) return 0;
+    Params pr;
+    if (!resolve(opts, m, n, &pr)) return 0;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); sms = 152; }
+    } else {
+        cudaGetLastError();
+    }
+    return make_layout(m, n, t_layout, pr, sms).total;
+}
+
+gbqr_status gbqr_sync(gbqr_ctx *cx, gbqr_info *info) {
+    if (!cx) return GBQR_EINVAL;
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    if (cudaStreamSynchronize(cx->stream) != cudaSuccess) return GBQR_ECUDA;
+    DeviceInfo h{0ull, LLONG_MAX};
+    if (cudaMemcpy(&h, cx->dinfo, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return GBQR_ECUDA;
+    DeviceInfo zero{0ull, LLONG_MAX};
+    if (cudaMemcpy(cx->dinfo, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return GBQR_ECUDA;
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->nonfinite = (int64_t)h.nonfinite;
+        info->rankdef_col = h.rankdef == LLONG_MAX ? -1 : (int64_t)h.rankdef;
+    }
+    return h.nonfinite ? GBQR_ENONFINITE : GBQR_OK;
+}
+
+gbqr_status gbqr_factor(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_t lda,
+                        double *T, int64_t ldt, int t_layout, const gbqr_opts *opts) {
+    if (!cx) return GBQR_EINVAL;
+    Params pr;
+    if (!resolve(opts, m, n, &pr)) return GBQR_EINVAL;
+    TRY(check_layout_args(m, n, lda, ldt, t_layout, pr.nb));
+    if (n == 0) return GBQR_OK;
+    if (!A || !T) return GBQR_EINVAL;
+    Work w;
+    TRY(begin_work(cx, m, n, t_layout, pr, &w));
+    const bool hostA = is_host_pointer(A), hostT = is_host_pointer(T);
+    if (hostA != hostT) return GBQR_EINVAL;
+    if (!hostA) return factor_device(w, m, n, A, lda, T, ldt, t_layout);
+    // host buffers: stage through the workspace, factor, copy back, synchronise
+    const int64_t trows = (t_layout == GBQR_T_FULL) ? n : std::min<int64_t>(pr.nb, n);
+    if ((size_t)trows * (size_t)n > w.L.n_bigT) return GBQR_ENOMEM;
+    if (cudaMemcpy2DAsync(w.bigA, m * 8, A, lda * 8, m * 8, n, cudaMemcpyHostToDevice, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    TRY(factor_device(w, m, n, w.bigA, m, w.bigT, trows, t_layout));
+    if (cudaMemcpy2DAsync(A, lda * 8, w.bigA, m * 8, m * 8, n, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    if (cudaMemcpy2DAsync(T, ldt * 8, w.bigT, trows * 8, trows * 8, n, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    return cudaStreamSynchronize(cx->stream) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+}
+
+static gbqr_status apply_entry(gbqr_ctx *cx, bool trans, int64_t m, int64_t n, const double *VR, int64_t lda,
+                               const double *T, int64_t ldt, int layout, int64_t nb, int64_t nrhs,
+                               double *B, int64_t ldb) {
+    if (!cx) return GBQR_EINVAL;
+    if (layout == GBQR_T_FULL) nb = std::max<int64_t>(n, 1);
+    TRY(check_layout_args(m, n, lda, ldt, layout, nb));
+    if (nrhs < 0 || ldb < std::max<int64_t>(1, m)) return GBQR_EINVAL;
+    if (n == 0 || nrhs == 0) return GBQR_OK;
+    if (!VR || !T || !B) return GBQR_EINVAL;
+    Params pr;
+    resolve(nullptr, m, n, &pr);
+    if (layout == GBQR_T_PANEL) pr.nb = nb;
+    Work w;
+    TRY(begin_work(cx, m, std::max(n, nrhs), layout, pr, &w));
+    if (layout == GBQR_T_FULL && (size_t)n * (size_t)nrhs > w.L.n_M) return GBQR_ENOMEM;
+    return apply_q_any(w, trans, m, n, VR, lda, T, ldt, layout, nb, nrhs, B, ldb, false);
+}
+
+gbqr_status gbqr_apply_qt(gbqr_ctx *cx, int64_t m, int64_t n, const double *VR, int64_t lda,
+                          const double *T, int64_t ldt, int t_layout, int64_t nb,
+                          int64_t nrhs, double *B, int64_t ldb) {
+    return apply_entry(cx, true, m, n, VR, lda, T, ldt, t_layout, nb, nrhs, B, ldb);
+}
+
+gbqr_status gbqr_apply_q(gbqr_ctx *cx, int64_t m, int64_t n, const double *VR, int64_t lda,
+                         const double *T, int64_t ldt, int t_layout, int64_t nb,
+                         int64_t nrhs, double *B, int64_t ldb) {
+    return apply_entry(cx, false, m, n, VR, lda, T, ldt, t_layout, nb, nrhs, B, ldb);
+}
+
+gbqr_status gbqr_form_q(gbqr_ctx *cx, int64_t m, int64_t n, const double *VR, int64_t lda,
+                        const double *T, int64_t ldt, int t_layout, int64_t nb,
+                        double *Q, int64_t ldq) {
+    if (!cx) return GBQR_EINVAL;
+    if (t_layout == GBQR_T_FULL) nb = std::max<int64_t>(n, 1);
+    TRY(check_layout_args(m, n, lda, ldt, t_layout, nb));
+    if (ldq < std::max<int64_t>(1, m)) return GBQR_EINVAL;
+    if (n == 0) return GBQR_OK;
+    if (!VR || !T || !Q) return GBQR_EINVAL;
+    Params pr;
+    resolve(nullptr, m, n, &pr);
+    if (t_layout == GBQR_T_PANEL) pr.nb = nb;
+    Work w;
+    TRY(begin_work(cx, m, n, t_layout, pr, &w));
+    TRY(fill_identity(w.ex, m, n, Q, ldq));
+    return apply_q_any(w, false, m, n, VR, lda, T, ldt, t_layout, nb, n, Q, ldq, true);
+}
+
+gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, int64_t lda,
+                          const double *b, double *x, int prec, gbqr_info *info) {
+    if (!cx) return GBQR_EINVAL;
+    if (prec != GBQR_FP64) return GBQR_EUNSUPPORTED;
+    if (m < n || n < 0 || lda < std::max<int64_t>(1, m)) return GBQR_EINVAL;
+    if (n == 0) return GBQR_OK;
+    if (!A || !b || !x) return GBQR_EINVAL;
+    Params pr;
+    resolve(nullptr, m, n, &pr);
+    Work w;
+    TRY(begin_work(cx, m, n, GBQR_T_PANEL, pr, &w));
+    const int64_t nb = std::min<int64_t>(pr.nb, n);
+    DeviceInfo *di = cx->dinfo;
+    static const long long kNone = LLONG_MAX;
+    if (cudaMemcpyAsync(&di->rankdef, &kNone, sizeof kNone, cudaMemcpyHostToDevice, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    TRY(copy_matrix(w.ex, m, n, A, lda, w.bigA, m));
+    TRY(factor_device(w, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL));
+    TRY(copy_matrix(w.ex, m, 1, b, m, w.vec, m));
+    TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, w.vec, m, false));
+    TRY(copy_matrix(w.ex, n, 1, w.vec, n, x, n));
+    TRY(trsv_upper(w.ex, n, w.bigA, m, x, &di->rankdef));
+    long long rk = -1;
+    if (cudaMemcpyAsync(&rk, &di->rankdef, sizeof rk, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    if (cudaStreamSynchronize(cx->stream) != cudaSuccess) return GBQR_ECUDA;
+    if (rk == LLONG_MAX) rk = -1;
+    if (info) {
+        memset(info, 0, sizeof *info);
+        info->rankdef_col = rk;
+    }
+    return rk >= 0 ? GBQR_ERANKDEF : GBQR_OK;
+}
+
+gbqr_status gbqr_trace_enable(gbqr_ctx *cx, int on) {
+    if (!cx || !cx->tracer) return GBQR_EINVAL;
+    cx->tracing = on != 0;
+    return GBQR_OK;
+}
+
+gbqr_status gbqr_trace_read(gbqr_ctx *cx, gbqr_trace_rec *out, int max, int *count) {
+    if (!cx || !cx->tracer || (max > 0 && !out)) return GBQR_EINVAL;
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    if (cudaStreamSynchronize(cx->stream) != cudaSuccess) return GBQR_ECUDA;
+    gbqr_trace_rec agg[FAM_COUNT];
+    memset(agg, 0, sizeof agg);
+    for (int f = 0; f < FAM_COUNT; ++f) strncpy(agg[f].name, kFamilyNames[f], sizeof agg[f].name - 1);
+    EventTracer *t = cx->tracer;
+    for (auto &r : t->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t->pool[r.e0], t->pool[r.e1]) != cudaSuccess) return GBQR_ECUDA;
+        agg[r.f].launches += 1;
+        agg[r.f].ms += ms;
+        agg[r.f].flops += r.flops;
+        agg[r.f].bytes += r.bytes;
+    }
+    t->recs.clear();
+    t->used = 0;
+    int c = 0;
+    for (int f = 0; f < FAM_COUNT && c < max; ++f)
+        if (agg[f].launches) out[c++] = agg[f];
+    if (count) *count = c;
+    return t->failed ? GBQR_ECUDA : GBQR_OK;
+}
+
+int64_t gbqr_launch_count(const gbqr_ctx *cx) { return cx ? cx->launches : 0; }
+
+}  // extern "C"

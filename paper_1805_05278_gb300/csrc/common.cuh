@@ -1,0 +1,117 @@
+// Internal declarations shared by the library's translation units.
+// Not part of the C ABI (see include/gbqr.h for that).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gbqr.h"
+
+namespace gbqr {
+
+constexpr int kThreads = 256;   // threads per CTA for every kernel family
+constexpr int kMaxPanel = 64;   // largest TSQR panel width w (= cutoff b)
+
+// ---------------------------------------------------------------- tracing
+enum Family { FAM_GEMM = 0, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TSQR_RECON, FAM_OTHER, FAM_COUNT };
+
+struct Tracer {
+    virtual void begin(cudaStream_t s, Family f) = 0;
+    virtual void end(cudaStream_t s, Family f, double flops, double bytes) = 0;
+    virtual ~Tracer() {}
+};
+
+// Everything a launcher needs besides its operands.
+struct Exec {
+    cudaStream_t stream = nullptr;
+    Tracer *tracer = nullptr;   // null = tracing off
+    int64_t *launches = nullptr;
+    int num_sms = 152;
+    int device = 0;
+};
+
+inline void trace_begin(const Exec &ex, Family f) {
+    if (ex.tracer) ex.tracer->begin(ex.stream, f);
+}
+inline gbqr_status trace_end(const Exec &ex, Family f, double flops, double bytes) {
+    if (ex.launches) ++*ex.launches;
+    if (ex.tracer) ex.tracer->end(ex.stream, f, flops, bytes);
+    return cudaPeekAtLastError() == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+}
+
+// ------------------------------------------------------------------ GEMM
+// Structural masks on a STORED operand (row r, column c of the array as laid
+// out in memory, before any transpose).
+enum Mask {
+    MASK_NONE = 0,
+    MASK_UNIT_LOWER = 1,  // r < c -> 0, r == c -> 1, r > c -> stored value (a V basis)
+    MASK_UPPER = 2        // r > c -> 0 (a T kernel or an R factor)
+};
+
+// C (M x N) = alpha * op(A) * op(B) + beta * C.
+//   ta == false: A stored M x K;  ta == true: A stored K x M, op(A) = A^T.
+//   B is stored K x N (no transpose needed by any caller).
+struct GemmOp {
+    int64_t M = 0, N = 0, K = 0;
+    const double *A = nullptr; int64_t lda = 1; bool ta = false; int maskA = MASK_NONE;
+    const double *B = nullptr; int64_t ldb = 1; int maskB = MASK_NONE;
+    double *C = nullptr; int64_t ldc = 1;
+    double alpha = 1.0, beta = 0.0;
+};
+
+// Scratch for split-K: partial tiles and self-resetting per-tile counters
+// (must be zero before the first use; every launch leaves them zero).
+struct GemmScratch {
+    double *partial = nullptr; size_t partial_elems = 0;
+    unsigned *counters = nullptr; size_t ncounters = 0;
+};
+
+size_t gemm_partial_elems_max(int num_sms);
+size_t gemm_counters_max(int num_sms);
+gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc);
+// Algorithmic flops of op (structural zeros of masked operands excluded).
+double gemm_algorithmic_flops(const GemmOp &op);
+
+// ------------------------------------------------------------------ TSQR
+// Base case of Algorithm 2: TSQR of an mp x w panel (Section 5, Appendix C).
+struct TsqrPlan {
+    int64_t mp = 0; int w = 0;
+    int P = 1;          // leaves (CTAs of the leaf stage)
+    int k = 2;          // tree fan-out
+    int L = 0;          // tree levels above the leaves
+    int hmax = 0;       // tallest leaf
+    int ldS = 0;        // up kernel shared-memory leading dimension (>= hmax, >= k*w)
+    int ldW = 0;        // down / recon kernels shared-memory leading dimension (>= hmax)
+    int64_t nodes = 0;  // leaves + internal nodes
+    size_t smem_up = 0, smem_down = 0, smem_recon = 0;
+    // workspace element counts
+    size_t nR = 0, nT = 0, nY = 0, nX = 0, ncount = 0;
+};
+
+struct TsqrWork {
+    double *R = nullptr, *T = nullptr, *Y = nullptr, *X = nullptr;
+    unsigned *counters = nullptr;   // zero before first use; left zero
+};
+
+// Plan for an mp x w panel.  leaf_rows = target leaf height (0 = default),
+// fanout in [2, 8].  Returns false if the panel cannot be planned.
+bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPlan *plan);
+// Worst-case plan sizes over panels of height <= mp and width <= w.
+TsqrPlan tsqr_plan_bound(int64_t mp, int w, int leaf_rows, int fanout, int num_sms);
+gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &plan, double *A, int64_t lda,
+                     double *Tout, int64_t ldt, const TsqrWork &work);
+
+// ------------------------------------------------------------ small kernels
+gbqr_status fill_identity(const Exec &ex, int64_t m, int64_t n, double *Q, int64_t ldq);
+gbqr_status zero_strict_lower(const Exec &ex, int64_t n, double *T, int64_t ldt);
+gbqr_status copy_matrix(const Exec &ex, int64_t m, int64_t n, const double *src, int64_t lds,
+                        double *dst, int64_t ldd);
+gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda,
+                           unsigned long long *flag);
+// x (n) <- R^{-1} x, R upper triangular n x n (ldr); records the first zero
+// diagonal index (or leaves *rankdef untouched) via atomicMin.
+gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x,
+                       long long *rankdef);
+
+}  // namespace gbqr

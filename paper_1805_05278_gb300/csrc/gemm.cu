@@ -1,0 +1,299 @@
+// FP64 GEMM for the update and T-assembly products of QR-EG (Algorithm 2):
+//   M1 = V_L^T A_R,  M2 = T_L^T M1,  A_R -= V_L M2          (update)
+//   M3 = V_L^T [0; V_R],  M4 = M3 T_R,  T12 = -T_L M4        (T assembly)
+// and the same three-product update for the right-looking top level
+// (Section 8.4) and for applying Q (basis-kernel update, Section 2.3).
+//
+// The operands carry structure that the paper's analysis deliberately
+// ignores (Section 2.3) but that costs real FP64 cycles here: V is unit lower
+// trapezoidal and T upper triangular.  The kernel masks them while staging
+// tiles and trims each tile's K range to the rows/columns that can be
+// non-zero, so triangular products cost about half of a dense one.
+//
+// Tall inner products (K = m, small M x N output) are split over K across
+// CTAs - the in-GPU form of the paper's K-split 1DMM followed by a Reduce
+// (Section 4, Lemma 3).  The partial tiles are summed by a fixed-shape tree
+// of "last CTA to arrive" reductions (fan-in 8): no CTA ever waits on
+// another, and the summation order is fixed, so results are deterministic.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace gbqr {
+namespace {
+
+constexpr int BK = 16;
+constexpr int kGroup = 8;   // fan-in of the split-K reduction tree
+
+struct GemmParams {
+    int64_t M, N, K;
+    const double *A; int64_t lda; int maskA;
+    const double *B; int64_t ldb; int maskB;
+    double *C; int64_t ldc;
+    double alpha, beta;
+    double *partial;          // per tile: slots_per_tile * BM*BN doubles
+    unsigned *counters;       // per tile: counters_per_tile
+    int slots_per_tile, counters_per_tile;
+};
+
+__device__ __forceinline__ double masked(const double *X, int64_t ld, int64_t r, int64_t c, int mask) {
+    if (mask == MASK_UNIT_LOWER) {
+        if (r < c) return 0.0;
+        if (r == c) return 1.0;
+    } else if (mask == MASK_UPPER) {
+        if (r > c) return 0.0;
+    }
+    return X[r + c * ld];
+}
+
+// K range [kb, ke) outside which op(A)(i, k) or op(B)(k, j) is structurally
+// zero for every i in [m0, m0+BM) and j in [n0, n0+BN).
+__device__ __forceinline__ void k_range(const GemmParams &p, bool ta, int64_t m0, int64_t n0,
+                                        int BM, int BN, int64_t &kb, int64_t &ke) {
+    kb = 0; ke = p.K;
+    if (p.maskA == MASK_UNIT_LOWER) {
+        if (!ta) ke = min(ke, m0 + BM);   // A(i,k) != 0 needs k <= i
+        else kb = max(kb, m0);            // A(k,i) != 0 needs k >= i
+    } else if (p.maskA == MASK_UPPER) {
+        if (!ta) kb = max(kb, m0);        // A(i,k) != 0 needs k >= i
+        else ke = min(ke, m0 + BM);       // A(k,i) != 0 needs k <= i
+    }
+    if (p.maskB == MASK_UNIT_LOWER) kb = max(kb, n0);       // B(k,j) != 0 needs k >= j
+    else if (p.maskB == MASK_UPPER) ke = min(ke, n0 + BN);  // B(k,j) != 0 needs k <= j
+}
+
+template <int BM, int BN, bool TA>
+__global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
+    constexpr int RM = BM / 16, RN = BN / 16;
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    const int S = gridDim.z, z = blockIdx.z;
+
+    int64_t kb, ke;
+    k_range(p, TA, m0, n0, BM, BN, kb, ke);
+    int64_t k_lo = kb, k_hi = kb;
+    if (ke > kb) {
+        int64_t chunk = (ke - kb + S - 1) / S;
+        chunk = (chunk + BK - 1) / BK * BK;
+        k_lo = kb + (int64_t)z * chunk;
+        k_hi = min(ke, k_lo + chunk);
+    }
+
+    double acc[RM][RN];
+#pragma unroll
+    for (int r = 0; r < RM; ++r)
+#pragma unroll
+        for (int c = 0; c < RN; ++c) acc[r][c] = 0.0;
+
+    for (int64_t k0 = k_lo; k0 < k_hi; k0 += BK) {
+        // op(A) tile: rows m0.., k0..
+#pragma unroll
+        for (int idx = tid; idx < BM * BK; idx += kThreads) {
+            int i, kk;
+            if (!TA) { i = idx % BM; kk = idx / BM; }   // coalesced along rows of stored A
+            else     { kk = idx % BK; i = idx / BK; }   // coalesced along rows of stored A (= k)
+            const int64_t gi = m0 + i, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < p.M && gk < k_hi) v = TA ? masked(p.A, p.lda, gk, gi, p.maskA)
+                                              : masked(p.A, p.lda, gi, gk, p.maskA);
+            As[kk][i] = v;
+        }
+        // B tile: stored K x N, coalesced along k
+#pragma unroll
+        for (int idx = tid; idx < BK * BN; idx += kThreads) {
+            const int kk = idx % BK, j = idx / BK;
+            const int64_t gk = k0 + kk, gj = n0 + j;
+            double v = 0.0;
+            if (gj < p.N && gk < k_hi) v = masked(p.B, p.ldb, gk, gj, p.maskB);
+            Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[RM], b[RN];
+#pragma unroll
+            for (int r = 0; r < RM; ++r) a[r] = As[kk][tx + 16 * r];
+#pragma unroll
+            for (int c = 0; c < RN; ++c) b[c] = Bs[kk][ty + 16 * c];
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < RN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+
+    if (S > 1) {
+        // Split-K: deterministic tree of last-arriver reductions.
+        const int64_t tile = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+        double *tp = p.partial + (size_t)tile * p.slots_per_tile * (BM * BN);
+        unsigned *tc = p.counters + (size_t)tile * p.counters_per_tile;
+        int slot = z, Sl = S, base = 0, cbase = 0;
+        for (;;) {
+            double *dst = tp + (size_t)(base + slot) * (BM * BN);
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < RN; ++c) dst[(tx + 16 * r) + (ty + 16 * c) * BM] = acc[r][c];
+            const int group = slot / kGroup, first = group * kGroup;
+            const int cnt = min(kGroup, Sl - first);
+            const int Snext = (Sl + kGroup - 1) / kGroup;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                unsigned prev = atomicAdd(&tc[cbase + group], 1u);
+                s_last = (prev == (unsigned)(cnt - 1));
+            }
+            __syncthreads();
+            if (!s_last) return;
+            __threadfence();
+            if (tid == 0) tc[cbase + group] = 0u;   // leave the counter zero for the next launch
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+#pragma unroll
+                for (int c = 0; c < RN; ++c) {
+                    double s = 0.0;
+                    for (int q = 0; q < cnt; ++q)
+                        s += __ldcg(tp + (size_t)(base + first + q) * (BM * BN) + (tx + 16 * r) + (ty + 16 * c) * BM);
+                    acc[r][c] = s;
+                }
+            if (Snext == 1) break;
+            base += Sl;
+            cbase += Snext;
+            slot = group;
+            Sl = Snext;
+        }
+    }
+
+#pragma unroll
+    for (int c = 0; c < RN; ++c) {
+        const int64_t gj = n0 + ty + 16 * c;
+        if (gj >= p.N) continue;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            const int64_t gi = m0 + tx + 16 * r;
+            if (gi >= p.M) continue;
+            double *cp = p.C + gi + gj * p.ldc;
+            double v = p.alpha * acc[r][c];
+            if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+            *cp = v;
+        }
+    }
+}
+
+int tile_for(int64_t d) { return d <= 16 ? 16 : (d <= 32 ? 32 : 64); }
+
+// Slots and counters per tile of the reduction tree for S splits.
+void tree_shape(int S, int *slots, int *counters) {
+    int s = 0, c = 0, Sl = S;
+    while (Sl > 1) {
+        s += Sl;
+        Sl = (Sl + kGroup - 1) / kGroup;
+        c += Sl;
+    }
+    *slots = std::max(s, 1);
+    *counters = std::max(c, 1);
+}
+
+template <int BM, int BN>
+cudaError_t launch_bm_bn(const GemmParams &p, bool ta, dim3 grid, cudaStream_t st) {
+    if (ta) dgemm_kernel<BM, BN, true><<<grid, kThreads, 0, st>>>(p);
+    else dgemm_kernel<BM, BN, false><<<grid, kThreads, 0, st>>>(p);
+    return cudaPeekAtLastError();
+}
+
+template <int BM>
+cudaError_t launch_bm(int BN, const GemmParams &p, bool ta, dim3 grid, cudaStream_t st) {
+    switch (BN) {
+        case 16: return launch_bm_bn<BM, 16>(p, ta, grid, st);
+        case 32: return launch_bm_bn<BM, 32>(p, ta, grid, st);
+        default: return launch_bm_bn<BM, 64>(p, ta, grid, st);
+    }
+}
+
+constexpr int kMaxSplitCtasPerSm = 4;
+
+}  // namespace
+
+size_t gemm_partial_elems_max(int num_sms) {
+    // at most kMaxSplitCtasPerSm*num_sms CTAs take part in split launches;
+    // the reduction tree adds < 1/7 more slots plus a few per tile.
+    size_t ctas = (size_t)kMaxSplitCtasPerSm * num_sms;
+    return (ctas * 2 + 64) * 64 * 64;
+}
+
+size_t gemm_counters_max(int num_sms) { return (size_t)kMaxSplitCtasPerSm * num_sms * 2 + 64; }
+
+double gemm_algorithmic_flops(const GemmOp &op) {
+    // 2*M*N*K for a dense product; a masked triangular operand halves its
+    // square part.  (Exact for the shapes used: the triangle is the leading
+    // square of the masked operand.)
+    double M = (double)op.M, N = (double)op.N, K = (double)op.K;
+    double f = 2.0 * M * N * K;
+    auto tri = [](double rows, double cols) {  // non-zero entries of a unit-lower/upper rows x cols
+        double s = std::min(rows, cols);
+        return rows * cols - s * (s - 1) / 2.0;
+    };
+    if (op.maskA != MASK_NONE) f = 2.0 * N * tri(op.ta ? K : M, op.ta ? M : K);
+    else if (op.maskB != MASK_NONE) f = 2.0 * M * tri(K, N);
+    return f;
+}
+
+gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc) {
+    if (op.M <= 0 || op.N <= 0) return GBQR_OK;
+    if (op.K <= 0) {
+        if (op.beta == 1.0) return GBQR_OK;
+    }
+    const int BM = tile_for(op.M), BN = tile_for(op.N);
+    const int64_t tm = (op.M + BM - 1) / BM, tn = (op.N + BN - 1) / BN;
+    if (tm > 0x7fffffff || tn > 65535) return GBQR_EUNSUPPORTED;
+    const int64_t tiles = tm * tn;
+    const int64_t ktiles = (std::max<int64_t>(op.K, 0) + BK - 1) / BK;
+
+    // Split K when the output alone cannot fill the GPU.  Each split keeps at
+    // least 4 K-tiles; pick the split count whose CTA total wastes the least
+    // of the last wave.
+    int S = 1;
+    const int64_t fill = 2LL * ex.num_sms;
+    if (tiles < fill && ktiles >= 8) {
+        const int64_t smax = std::min<int64_t>({ktiles / 4, (int64_t)kMaxSplitCtasPerSm * ex.num_sms / tiles, 512});
+        double best = -1.0;
+        for (int64_t s = 1; s <= smax; ++s) {
+            const double ctas = (double)(tiles * s);
+            const double waves = std::ceil(ctas / ex.num_sms);
+            // useful fraction of the occupied SM-waves, lightly favouring more parallelism
+            const double eff = ctas / (waves * ex.num_sms) * std::min(1.0, ctas / (double)fill);
+            if (eff > best + 1e-9) { best = eff; S = (int)s; }
+        }
+    }
+    GemmParams p;
+    p.M = op.M; p.N = op.N; p.K = std::max<int64_t>(op.K, 0);
+    p.A = op.A; p.lda = op.lda; p.maskA = op.maskA;
+    p.B = op.B; p.ldb = op.ldb; p.maskB = op.maskB;
+    p.C = op.C; p.ldc = op.ldc; p.alpha = op.alpha; p.beta = op.beta;
+    p.partial = sc.partial; p.counters = sc.counters;
+    p.slots_per_tile = 1; p.counters_per_tile = 1;
+    if (S > 1) {
+        tree_shape(S, &p.slots_per_tile, &p.counters_per_tile);
+        size_t need_p = (size_t)tiles * p.slots_per_tile * BM * BN;
+        size_t need_c = (size_t)tiles * p.counters_per_tile;
+        if (need_p > sc.partial_elems || need_c > sc.ncounters || !sc.partial || !sc.counters) return GBQR_ENOMEM;
+    }
+    dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)S);
+    trace_begin(ex, FAM_GEMM);
+    cudaError_t e;
+    switch (BM) {
+        case 16: e = launch_bm<16>(BN, p, op.ta, grid, ex.stream); break;
+        case 32: e = launch_bm<32>(BN, p, op.ta, grid, ex.stream); break;
+        default: e = launch_bm<64>(BN, p, op.ta, grid, ex.stream); break;
+    }
+    if (e != cudaSuccess) return GBQR_ECUDA;
+    const double bytes = 8.0 * ((double)op.M * op.K + (double)op.K * op.N + (op.beta != 0.0 ? 2.0 : 1.0) * op.M * op.N);
+    return trace_end(ex, FAM_GEMM, gemm_algorithmic_flops(op), bytes);
+}
+
+}  // namespace gbqr

@@ -1,0 +1,172 @@
+"""GPU parity of gbqr_factor (QR-EG with TSQR base case) with the CPU oracle:
+V, T and R element by element on seeded inputs, across shapes (ragged tails,
+square, n = 1, tiny), both T layouts, and the algorithm's tunables (cutoff b,
+leaf height, tree fan-out, panel width) - R must not depend on them."""
+
+import numpy as np
+import pytest
+
+import workloads
+from tests import _gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(gb):
+    c = gb.Context(0)
+    yield c
+    c.close()
+
+
+SHAPES = [
+    # (m, n, seed, graded)
+    (1024, 128, 0, False),   # the small named workload
+    (1000, 77, 1, False),    # ragged: leaves and panels do not divide
+    (333, 33, 2, True),
+    (64, 64, 3, False),      # square
+    (129, 65, 4, True),
+    (7, 1, 5, False),        # n = 1
+    (5, 3, 6, False),        # tiny
+    (1, 1, 7, False),
+    (4096, 1, 8, False),
+    (2000, 5, 9, True),
+    (300, 300, 10, True),
+]
+
+
+@pytest.mark.parametrize("m,n,seed,graded", SHAPES)
+@pytest.mark.parametrize("layout_name", ["full", "panel"])
+def test_factor_matches_oracle(gb, ctx, orc, m, n, seed, graded, layout_name):
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    a = workloads.graded(m, n, seed) if graded else workloads.gaussian(m, n, seed)
+    VR, T, nb = _gpu.factor_gpu(ctx, a, layout)
+    _gpu.compare_factor(a, VR, T, layout, nb, orc, f"{m}x{n} {layout_name}")
+
+
+TUNABLES = [
+    # cutoff_b, panel_nb, leaf_rows, fanout
+    (1, 0, 0, 2),
+    (2, 0, 0, 3),
+    (3, 0, 7, 2),
+    (16, 0, 16, 4),
+    (32, 50, 100, 8),
+    (64, 64, 0, 2),
+    (64, 0, 256, 5),
+    (8, 16, 33, 2),
+]
+
+
+@pytest.mark.parametrize("b,nb,leaf,k", TUNABLES)
+@pytest.mark.parametrize("layout_name", ["full", "panel"])
+def test_tunables_do_not_change_the_result(gb, ctx, orc, b, nb, leaf, k, layout_name):
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    a = workloads.gaussian(777, 97, 11)
+    o = gb.opts(cutoff_b=b, panel_nb=nb, leaf_rows=leaf, fanout=k)
+    VR, T, nbr = _gpu.factor_gpu(ctx, a, layout, o)
+    _gpu.compare_factor(a, VR, T, layout, nbr, orc, f"b={b} nb={nb} leaf={leaf} k={k}")
+
+
+def test_pure_tsqr_base_case(gb, ctx, orc):
+    """b >= n: QR-EG is one TSQR (the 1D-CAQR-EG b = n case)."""
+    a = workloads.gaussian(5000, 48, 12)
+    for k in (2, 3, 8):
+        o = gb.opts(cutoff_b=64, leaf_rows=64, fanout=k)
+        VR, T, nb = _gpu.factor_gpu(ctx, a, gb.GBQR_T_FULL, o)
+        _gpu.compare_factor(a, VR, T, gb.GBQR_T_FULL, nb, orc, f"tsqr k={k}")
+
+
+def test_single_leaf(gb, ctx, orc):
+    """P = 1: TSQR reduces to one local QR plus the reconstruction."""
+    a = workloads.gaussian(40, 32, 13)
+    o = gb.opts(cutoff_b=32, leaf_rows=4000)
+    VR, T, nb = _gpu.factor_gpu(ctx, a, gb.GBQR_T_FULL, o)
+    _gpu.compare_factor(a, VR, T, gb.GBQR_T_FULL, nb, orc, "single leaf")
+
+
+def test_odd_leading_dimension(gb, ctx, orc):
+    a = workloads.graded(513, 70, 14)
+    for pad in (1, 3, 8):
+        VR, T, nb = _gpu.factor_gpu(ctx, a, gb.GBQR_T_PANEL, None, lda_pad=pad)
+        _gpu.compare_factor(a, VR, T, gb.GBQR_T_PANEL, nb, orc, f"lda pad {pad}")
+
+
+def test_upper_triangular_input(gb, ctx, orc):
+    """Zero subcolumns: every reflector is I - 2 e_j e_j^T, so R = -A exactly
+    in structure and V has no entries below the diagonal."""
+    a = workloads.upper_triangular(300, 40, 15)
+    VR, T, nb = _gpu.factor_gpu(ctx, a, gb.GBQR_T_FULL, gb.opts(cutoff_b=16))
+    _gpu.compare_factor(a, VR, T, gb.GBQR_T_FULL, nb, orc, "upper triangular")
+
+
+def test_zero_column_gives_a_valid_qr(gb, ctx):
+    """Rank deficiency: V, T are not unique, so check A = QR and Q^T Q = I."""
+    import torch
+    a = workloads.gaussian(400, 30, 16)
+    a[:, 7] = 0.0
+    A = _gpu.device_matrix(a)
+    T = _gpu.t_buffer(30, gb.GBQR_T_FULL, 30)
+    ctx.factor(A, T, gb.GBQR_T_FULL, gb.opts(cutoff_b=8))
+    Q = gb.colmajor(400, 30)
+    ctx.form_q(A, T, Q, gb.GBQR_T_FULL)
+    torch.cuda.synchronize()
+    q = gb.to_numpy(Q)
+    r = np.triu(gb.to_numpy(A)[:30])
+    assert np.isfinite(q).all() and np.isfinite(r).all()
+    assert np.linalg.norm(a - q @ r) / np.linalg.norm(a) <= _gpu.TOL_BACKWARD
+    assert np.linalg.norm(q.T @ q - np.eye(30)) <= _gpu.TOL_BACKWARD
+    assert abs(r[7, 7]) <= 1e-13 * np.linalg.norm(a)
+
+
+def test_deterministic(gb, ctx):
+    """Fixed tree and split shapes: two runs are bit-identical."""
+    a = workloads.graded(3000, 200, 17)
+    r1 = _gpu.factor_gpu(ctx, a, gb.GBQR_T_PANEL)
+    r2 = _gpu.factor_gpu(ctx, a, gb.GBQR_T_PANEL)
+    assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1])
+
+
+def test_nonfinite_input_is_reported(gb, ctx):
+    import torch
+    a = workloads.gaussian(200, 20, 18)
+    a[13, 4] = np.nan
+    ctx.sync()
+    A = _gpu.device_matrix(a)
+    T = _gpu.t_buffer(20, gb.GBQR_T_PANEL, 20)
+    ctx.factor(A, T, gb.GBQR_T_PANEL)
+    st, info = ctx.sync()
+    assert st == gb.GBQR_ENONFINITE and info.nonfinite
+    st, info = ctx.sync()
+    assert st == gb.GBQR_OK
+    torch.cuda.synchronize()
+
+
+def test_invalid_arguments(gb, ctx):
+    import ctypes
+    A = gb.colmajor(10, 20)
+    T = gb.colmajor(20, 20)
+    h = ctx.handle
+    P = ctypes.c_void_p
+    assert gb.gbqr_factor(h, 10, 20, P(A.data_ptr()), 10, P(T.data_ptr()), 20, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
+    A = gb.colmajor(30, 20)
+    assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 29, P(T.data_ptr()), 20, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
+    assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 30, P(T.data_ptr()), 19, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
+    assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 30, P(T.data_ptr()), 20, 5, None) == gb.GBQR_EINVAL
+    bad = gb.opts(cutoff_b=65)
+    assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 30, P(T.data_ptr()), 20, gb.GBQR_T_FULL, ctypes.byref(bad)) == gb.GBQR_EINVAL
+    bad = gb.opts(fanout=1)
+    assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 30, P(T.data_ptr()), 20, gb.GBQR_T_FULL, ctypes.byref(bad)) == gb.GBQR_EINVAL
+    # n = 0 is a no-op
+    assert gb.gbqr_factor(h, 30, 0, P(A.data_ptr()), 30, P(T.data_ptr()), 1, gb.GBQR_T_FULL, None) == gb.GBQR_OK
+
+
+def test_host_pointers(gb, ctx, orc):
+    """A and T in host memory: the call stages through the device."""
+    import ctypes
+    a = workloads.gaussian(600, 50, 19)
+    vr = np.asfortranarray(a.copy())
+    t = np.zeros((50, 50), order="F")
+    st = gb.gbqr_factor(ctx.handle, 600, 50, vr.ctypes.data_as(ctypes.c_void_p), 600,
+                        t.ctypes.data_as(ctypes.c_void_p), 50, gb.GBQR_T_FULL, None)
+    assert st == gb.GBQR_OK
+    _gpu.compare_factor(a, vr, t, gb.GBQR_T_FULL, 50, orc, "host pointers")
