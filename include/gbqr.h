@@ -210,6 +210,36 @@ GBQR_API gbqr_status gbqr_trace_read(gbqr_ctx *ctx, gbqr_trace_rec *out, int max
 /* Number of kernel launches the context has issued since creation. */
 GBQR_API int64_t gbqr_launch_count(const gbqr_ctx *ctx);
 
+/* ---- allocation-free tall-skinny QR ------------------------------------ */
+
+/* QR of a tall-skinny m x n matrix (n <= 32, m >= n) with no device
+ * allocation and no context: the same TSQR kernels as the base case of
+ * gbqr_factor (leaf QR, merge tree, downsweep, reconstruction), with the
+ * tree's scratch in a fixed 16 MiB static device array instead of a
+ * workspace.  The paper has no counterpart to this entry point.
+ *
+ * For callers that cannot call cudaMalloc: code that must not synchronise
+ * the device (cudaMalloc/cudaFree can serialise with every stream), code
+ * whose allocator owns the device memory budget and must see every byte,
+ * and deployments that fix their device footprint at load time.  The caller
+ * passes its input and outputs only.
+ *   A (m x n, lda >= m): in: A; out: V (strict lower, unit diagonal implied)
+ *                        and R (upper triangle), as gbqr_factor.
+ *   T (n x n, ldt >= n): out: the n x n upper triangular kernel, zeros below.
+ *   cuda_stream:         the cudaStream_t to enqueue on (asynchronous).
+ * Every GPU that loads this library holds the 16 MiB array until the
+ * process exits.  All calls share it and it keeps the last call's contents;
+ * each call clears the tree's arrival counters itself.  Calls that overlap on
+ * the GPU (other streams, other host threads) race on the array: serialise
+ * them.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Sizes whose reduction tree does not fit the
+ * array (leaves grown up to the shared-memory limit first), n > 32, m < n or
+ * too small leading dimensions return EINVAL before any CUDA call.
+ * Errors: EINVAL, ECUDA, EUNSUPPORTED (device index >= 64). */
+GBQR_API gbqr_status gbqr_tsqr_static(int64_t m, int64_t n, double *A, int64_t lda,
+                                      double *T, int64_t ldt, void *cuda_stream);
+
 /* ---- diagnostics -------------------------------------------------------- */
 
 /* Measure the FP64 FMA throughput of CUDA device `device`: kind 0 = DFMA on

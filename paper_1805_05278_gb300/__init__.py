@@ -65,6 +65,7 @@ SIGNATURES = {
     "gbqr_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gbqr_trace_read": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_trace_rec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_launch_count": (_I64, [_P]),
+    "gbqr_tsqr_static": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
     "gbqr_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gbqr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
