@@ -89,7 +89,10 @@ typedef struct {
     int32_t leaf_rows;  /* TSQR leaf height target m_p (>= b; Section 5 needs m_p >= n) */
     int32_t fanout;     /* TSQR reduction-tree fan-out k (2..8; the paper's
                            binomial tree is k = 2, Appendix C.1) */
-    int32_t reserved[4];
+    int32_t lookahead;  /* GBQR_T_PANEL: 0 or 1 = factor panel k+1 on a
+                           high-priority internal stream while the rest of
+                           panel k's trailing update runs (default); -1 = off */
+    int32_t reserved[3];
 } gbqr_opts;
 
 /* Device-side record of one or more calls since the last gbqr_sync(). */

@@ -35,7 +35,7 @@ _P = ctypes.c_void_p
 class gbqr_opts(ctypes.Structure):
     _fields_ = [("cutoff_b", ctypes.c_int32), ("panel_nb", ctypes.c_int32),
                 ("leaf_rows", ctypes.c_int32), ("fanout", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("lookahead", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class gbqr_info(ctypes.Structure):
@@ -113,9 +113,11 @@ def check(status: int, what: str) -> int:
     return status
 
 
-def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int = 0) -> gbqr_opts:
+def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int = 0,
+         lookahead: int = 0) -> gbqr_opts:
     o = gbqr_opts()
     o.cutoff_b, o.panel_nb, o.leaf_rows, o.fanout = cutoff_b, panel_nb, leaf_rows, fanout
+    o.lookahead = lookahead
     return o
 
 

@@ -20,7 +20,7 @@ using namespace gbqr;
 namespace {
 
 constexpr int kDefaultCutoff = 32;
-constexpr int kDefaultFanout = 2;
+constexpr int kDefaultFanout = 0;   // 0: the TSQR planner chooses
 constexpr int64_t kDefaultPanel = 128;
 
 struct DeviceInfo {
@@ -68,6 +68,7 @@ struct Params {
     int64_t nb = kDefaultPanel;
     int leaf_rows = 0;
     int fanout = kDefaultFanout;
+    bool lookahead = true;
 };
 
 bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
@@ -81,6 +82,8 @@ bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
         if (o->panel_nb) r.nb = o->panel_nb;
         if (o->leaf_rows) r.leaf_rows = o->leaf_rows;
         if (o->fanout) r.fanout = o->fanout;
+        if (o->lookahead < -1 || o->lookahead > 1) return false;
+        if (o->lookahead == -1) r.lookahead = false;
     }
     r.nb = std::max<int64_t>(1, r.nb);
     *p = r;
@@ -91,8 +94,9 @@ bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
 struct Layout {
     size_t partial = 0, gcount = 0, tR = 0, tT = 0, tY = 0, tX = 0, tcount = 0;
     size_t M1 = 0, M2 = 0, bigA = 0, bigT = 0, vec = 0;
+    size_t partial2 = 0, gcount2 = 0, M1b = 0, M2b = 0;   // second lane (look-ahead panel stream)
     size_t total = 0;
-    size_t n_partial = 0, n_gcount = 0, n_M = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
+    size_t n_partial = 0, n_gcount = 0, n_M = 0, n_Mb = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
     TsqrPlan tsqr;
 };
 
@@ -122,6 +126,12 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     L.tX = take(L.tsqr.nX * 8);
     L.M1 = take(nM * 8);
     L.M2 = take(nM * 8);
+    // second lane: panel factorizations of width <= nb run there
+    L.n_Mb = std::max<size_t>((size_t)nb * (size_t)nb, 16);
+    L.partial2 = take(L.n_partial * 8);
+    L.gcount2 = take(align_up(L.n_gcount * 4, 16));
+    L.M1b = take(L.n_Mb * 8);
+    L.M2b = take(L.n_Mb * 8);
     L.bigA = take(L.n_bigA * 8);
     L.bigT = take(L.n_bigT * 8);
     L.vec = take((size_t)std::max<int64_t>(m, 1) * 8);
@@ -142,6 +152,8 @@ struct gbqr_ctx {
     int64_t launches = 0;
     EventTracer *tracer = nullptr;
     bool tracing = false;
+    cudaStream_t side = nullptr;          // high-priority stream for look-ahead panels
+    cudaEvent_t ev_panel = nullptr, ev_ready = nullptr, ev_fork = nullptr;
 
     Exec exec() {
         Exec e;
@@ -165,6 +177,21 @@ struct Work {
     GemmScratch gs;
     TsqrWork tw;
     double *M1, *M2, *bigA, *bigT, *vec;
+    size_t n_M;                      // capacity of M1 / M2 of this lane
+    GemmScratch gs2;
+    double *M1b, *M2b;
+
+    // The second lane: same TSQR workspace, its own GEMM scratch and
+    // temporaries, enqueued on the context's side stream.
+    Work lane2() const {
+        Work o = *this;
+        o.ex.stream = cx->side;
+        o.gs = gs2;
+        o.M1 = M1b;
+        o.M2 = M2b;
+        o.n_M = L.n_Mb;
+        return o;
+    }
 };
 
 gbqr_status ensure_workspace(gbqr_ctx *cx, size_t bytes) {
@@ -172,6 +199,7 @@ gbqr_status ensure_workspace(gbqr_ctx *cx, size_t bytes) {
     if (!cx->ws_owned) return GBQR_ENOMEM;
     if (cx->ws) {
         cudaStreamSynchronize(cx->stream);
+        if (cx->side) cudaStreamSynchronize(cx->side);
         cudaFree(cx->ws);
         cx->ws = nullptr;
         cx->ws_bytes = 0;
@@ -206,8 +234,17 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
     w->bigA = (double *)(base + w->L.bigA);
     w->bigT = (double *)(base + w->L.bigT);
     w->vec = (double *)(base + w->L.vec);
+    w->n_M = w->L.n_M;
+    w->gs2.partial = (double *)(base + w->L.partial2);
+    w->gs2.partial_elems = w->L.n_partial;
+    w->gs2.counters = (unsigned *)(base + w->L.gcount2);
+    w->gs2.ncounters = w->L.n_gcount;
+    w->M1b = (double *)(base + w->L.M1b);
+    w->M2b = (double *)(base + w->L.M2b);
     // arrival counters start at zero (every kernel leaves them zero again)
     if (cudaMemsetAsync(base + w->L.gcount, 0, w->L.counter_bytes, cx->stream) != cudaSuccess)
+        return GBQR_ECUDA;
+    if (cudaMemsetAsync(base + w->L.gcount2, 0, align_up(w->L.n_gcount * 4, 16), cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
     return GBQR_OK;
 }
@@ -219,7 +256,7 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
 gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
                         const double *V, int64_t ldv, const double *T, int64_t ldt, double *C, int64_t ldc) {
     if (mr <= 0 || nc <= 0 || kv <= 0) return GBQR_OK;
-    if ((size_t)kv * (size_t)nc > w.L.n_M) return GBQR_ENOMEM;
+    if ((size_t)kv * (size_t)nc > w.n_M) return GBQR_ENOMEM;
     GemmOp g;
     g.M = kv; g.N = nc; g.K = mr;
     g.A = V; g.lda = ldv; g.ta = true; g.maskA = MASK_UNIT_LOWER;
@@ -259,7 +296,7 @@ gbqr_status qr_eg(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double 
     double *TR = T + n1 + n1 * ldt;
     TRY(qr_eg(w, m - n1, n2, A + n1 + n1 * lda, lda, TR, ldt));
     // M3 = V_L(n1:m, :)^T V_R ; M4 = M3 T_R ; T12 = -T_L M4
-    if ((size_t)n1 * (size_t)n2 > w.L.n_M) return GBQR_ENOMEM;
+    if ((size_t)n1 * (size_t)n2 > w.n_M) return GBQR_ENOMEM;
     GemmOp g3;
     g3.M = n1; g3.N = n2; g3.K = m - n1;
     g3.A = A + n1; g3.lda = lda; g3.ta = true; g3.maskA = MASK_NONE;
@@ -307,13 +344,44 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda,
     }
     const int64_t nb = std::min<int64_t>(w.pr.nb, n);
     TRY(zero_below_blocks(w, nb, n, nb, T, ldt));
-    for (int64_t j0 = 0; j0 < n; j0 += nb) {
-        const int64_t wd = std::min<int64_t>(nb, n - j0);
-        double *Ap = A + j0 + j0 * lda;
-        double *Tk = T + j0 * ldt;
-        TRY(qr_eg(w, m - j0, wd, Ap, lda, Tk, ldt));
-        if (j0 + wd < n)
-            TRY(apply_block(w, true, m - j0, n - j0 - wd, wd, Ap, lda, Tk, ldt, A + j0 + (j0 + wd) * lda, lda));
+    const int64_t npan = (n + nb - 1) / nb;
+    gbqr_ctx *cx = w.cx;
+    if (!w.pr.lookahead || npan == 1 || !cx->side) {
+        for (int64_t j0 = 0; j0 < n; j0 += nb) {
+            const int64_t wd = std::min<int64_t>(nb, n - j0);
+            double *Ap = A + j0 + j0 * lda;
+            double *Tk = T + j0 * ldt;
+            TRY(qr_eg(w, m - j0, wd, Ap, lda, Tk, ldt));
+            if (j0 + wd < n)
+                TRY(apply_block(w, true, m - j0, n - j0 - wd, wd, Ap, lda, Tk, ldt, A + j0 + (j0 + wd) * lda, lda));
+        }
+        return GBQR_OK;
+    }
+    // Look-ahead (depth 1): panel k+1 is factored on the high-priority side
+    // stream while the rest of panel k's trailing update runs on the main
+    // stream.  Event fork/join only, so the sequence is graph-capturable.
+    Work wp = w.lane2();
+    const cudaStream_t ms = w.ex.stream, ss = cx->side;
+    if (cudaEventRecord(cx->ev_fork, ms) != cudaSuccess || cudaStreamWaitEvent(ss, cx->ev_fork, 0) != cudaSuccess)
+        return GBQR_ECUDA;
+    TRY(qr_eg(wp, m, std::min<int64_t>(nb, n), A, lda, T, ldt));
+    if (cudaEventRecord(cx->ev_panel, ss) != cudaSuccess) return GBQR_ECUDA;
+    for (int64_t k = 0; k < npan; ++k) {
+        const int64_t j0 = k * nb, wd = std::min<int64_t>(nb, n - j0);
+        if (cudaStreamWaitEvent(ms, cx->ev_panel, 0) != cudaSuccess) return GBQR_ECUDA;   // panel k done
+        if (k + 1 == npan) break;
+        const int64_t j1 = j0 + wd, w1 = std::min<int64_t>(nb, n - j1);
+        const double *Vk = A + j0 + j0 * lda;
+        const double *Tk = T + j0 * ldt;
+        // panel k+1's columns first ...
+        TRY(apply_block(w, true, m - j0, w1, wd, Vk, lda, Tk, ldt, A + j0 + j1 * lda, lda));
+        if (cudaEventRecord(cx->ev_ready, ms) != cudaSuccess || cudaStreamWaitEvent(ss, cx->ev_ready, 0) != cudaSuccess)
+            return GBQR_ECUDA;
+        // ... then panel k+1 on the side stream, concurrently with the rest of the update
+        TRY(qr_eg(wp, m - j1, w1, A + j1 + j1 * lda, lda, T + j1 * ldt, ldt));
+        if (cudaEventRecord(cx->ev_panel, ss) != cudaSuccess) return GBQR_ECUDA;
+        if (j1 + w1 < n)
+            TRY(apply_block(w, true, m - j0, n - j1 - w1, wd, Vk, lda, Tk, ldt, A + j0 + (j1 + w1) * lda, lda));
     }
     return GBQR_OK;
 }
@@ -407,6 +475,16 @@ gbqr_status gbqr_create(gbqr_ctx **out, int device, void *cuda_stream) {
         return GBQR_ECUDA;
     }
     cx->tracer = new (std::nothrow) EventTracer();
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&cx->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cx->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        gbqr_destroy(cx);
+        return GBQR_ECUDA;
+    }
     *out = cx;
     return GBQR_OK;
 }
@@ -415,8 +493,14 @@ gbqr_status gbqr_destroy(gbqr_ctx *cx) {
     if (!cx) return GBQR_EINVAL;
     cudaSetDevice(cx->device);
     cudaStreamSynchronize(cx->stream);
+    if (cx->side) cudaStreamSynchronize(cx->side);
     if (cx->ws_owned && cx->ws) cudaFree(cx->ws);
+    cx->ws = nullptr;
     if (cx->dinfo) cudaFree(cx->dinfo);
+    if (cx->ev_panel) cudaEventDestroy(cx->ev_panel);
+    if (cx->ev_ready) cudaEventDestroy(cx->ev_ready);
+    if (cx->ev_fork) cudaEventDestroy(cx->ev_fork);
+    if (cx->side) cudaStreamDestroy(cx->side);
     delete cx->tracer;
     delete cx;
     return GBQR_OK;
@@ -433,6 +517,7 @@ gbqr_status gbqr_set_workspace(gbqr_ctx *cx, void *ptr, size_t bytes) {
     if (ptr && ((uintptr_t)ptr % 16) != 0) return GBQR_EINVAL;
     if (cx->ws_owned && cx->ws) {
         cudaStreamSynchronize(cx->stream);
+        if (cx->side) cudaStreamSynchronize(cx->side);
         cudaFree(cx->ws);
     }
     cx->ws = (char *)ptr;

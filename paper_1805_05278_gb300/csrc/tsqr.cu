@@ -40,22 +40,37 @@ struct TsqrParams {
     double *Tout; int64_t ldt;
 };
 
+constexpr unsigned kFull = 0xffffffffu;
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
-// Sum over the CTA; every thread receives the same value (fixed order).
-__device__ double block_sum(double v, double *red) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    double s = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
-    return s;
+// Warp sums of N <= 4 per-lane values; every lane receives all N sums.  For
+// N > 1 a butterfly reduce-scatter (halve the set at offsets 16 and 8, then
+// three full stages) costs 6 FP64 adds instead of 5 per value.
+template <int N>
+__device__ __forceinline__ void warp_sum_n(double (&v)[4]) {
+    if (N == 1) { v[0] = warp_sum(v[0]); return; }
+    const int lane = threadIdx.x & 31;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    double k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
+    const double s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
+    k0 += __shfl_xor_sync(kFull, s0, 16);
+    k1 += __shfl_xor_sync(kFull, s1, 16);
+    double k = h8 ? k1 : k0;
+    const double s = h8 ? k0 : k1;
+    k += __shfl_xor_sync(kFull, s, 8);
+    k += __shfl_xor_sync(kFull, k, 4);
+    k += __shfl_xor_sync(kFull, k, 2);
+    k += __shfl_xor_sync(kFull, k, 1);
+    // lane L now holds sum number 2*bit4(L) + bit3(L)
+    v[0] = __shfl_sync(kFull, k, 0);
+    v[1] = __shfl_sync(kFull, k, 8);
+    v[2] = __shfl_sync(kFull, k, 16);
+    v[3] = __shfl_sync(kFull, k, 24);
 }
 
 __device__ __forceinline__ int64_t leaf_begin(int64_t mp, int P, int p) { return (int64_t)p * mp / P; }
@@ -63,100 +78,163 @@ __device__ __forceinline__ int64_t leaf_begin(int64_t mp, int P, int p) { return
 // Rows of column j below its pivot in a leaf block: j+1 .. h-1.
 struct LeafRows {
     int h;
-    __device__ int count(int j) const { return h - j - 1; }
-    __device__ int row(int j, int idx) const { return j + 1 + idx; }
+    template <class F>
+    __device__ __forceinline__ void each(int j, int lane, F &&f) const {
+        for (int r = j + 1 + lane; r < h; r += 32) f(r);
+    }
 };
 
 // Rows of column j below its pivot in cnt stacked w x w upper triangles:
 // rows 0..j of every triangle after the first.
 struct MergeRows {
     int w, cnt;
-    __device__ int count(int j) const { return (cnt - 1) * (j + 1); }
-    __device__ int row(int j, int idx) const {
-        const int i = idx / (j + 1);
-        return (i + 1) * w + (idx - i * (j + 1));
+    template <class F>
+    __device__ __forceinline__ void each(int j, int lane, F &&f) const {
+        for (int i = 1; i < cnt; ++i)
+            for (int r = lane; r <= j; r += 32) f(i * w + r);
     }
 };
 
-// Householder QR of the w columns held in shared memory S (column-major,
-// leading dimension ldS), column j acting on its pivot row j and the rows
-// that `rows` lists.  On return: R on and above the pivots, the vectors'
-// entries below them (unit pivot implied), tau[0:w], and T (w x w, ld w,
-// zero below the diagonal) by the forward recurrence
-// T(0:j, j) = -tau_j T(0:j, 0:j) (V(:, 0:j)^T v_j).  The inner products
-// v_c^T v_j for c < j come from the same pass that updates columns c > j.
-// Sign convention: beta = -sgn(alpha) * ||column||, sgn(0) = +1; a zero
-// column gives v = e_j, tau = 2.
+// One warp turns column c into a Householder reflector: beta on the pivot,
+// the scaled vector below it, tau[c].  beta = -sgn(alpha) ||column||,
+// sgn(0) = +1, no exception for a reduced column (tau = 2); a zero column
+// gives v = e_c, tau = 2.  With d = alpha - beta (no cancellation) and
+// q = 1 / (beta d): scale = 1/d = beta q and tau = (beta - alpha)/beta = -d^2 q,
+// so the pivot costs one square root and one reciprocal.
 template <class Rows>
-__device__ void householder_block(double *S, int ldS, int w, Rows rows, double *tau, double *T,
-                                  double *red, double *z) {
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int nthr = blockDim.x, nw = nthr >> 5;
-    for (int i = tid; i < w * w; i += nthr) T[i] = 0.0;
-    for (int j = 0; j < w; ++j) {
-        const int cnt = rows.count(j);
-        double *colj = S + (size_t)j * ldS;
-        double part = 0.0;
-        for (int idx = tid; idx < cnt; idx += nthr) {
-            const double x = colj[rows.row(j, idx)];
-            part = fma(x, x, part);
-        }
-        const double sig2 = block_sum(part, red);   // ends with __syncthreads
-        const double alpha = colj[j];
-        const double nrm = sqrt(fma(alpha, alpha, sig2));
-        const double beta = alpha < 0.0 ? nrm : -nrm;
-        double tj, scal;
-        if (beta == 0.0) { tj = 2.0; scal = 0.0; }
-        else { tj = (beta - alpha) / beta; scal = 1.0 / (alpha - beta); }
-        __syncthreads();   // every thread has read alpha
-        if (tid == 0) { colj[j] = beta; tau[j] = tj; }
-        if (beta != 0.0)
-            for (int idx = tid; idx < cnt; idx += nthr) colj[rows.row(j, idx)] *= scal;
-        __syncthreads();
-        // one warp per other column: s_c = A(j,c) + sum_r v_j(r) A(r,c)
-        for (int c = wid; c < w; c += nw) {
-            if (c == j) continue;
+__device__ void warp_pivot(double *S, int ldS, int c, const Rows &rows, double *tau) {
+    const int lane = threadIdx.x & 31;
+    double *col = S + (size_t)c * ldS;
+    double part = 0.0;
+    rows.each(c, lane, [&](int r) { const double x = col[r]; part = fma(x, x, part); });
+    const double sig2 = warp_sum(part);
+    const double alpha = col[c];
+    const double nrm = sqrt(fma(alpha, alpha, sig2));
+    const double beta = alpha < 0.0 ? nrm : -nrm;
+    double tj = 2.0;
+    if (beta != 0.0) {
+        const double d = alpha - beta;
+        const double q = 1.0 / (beta * d);
+        const double scal = beta * q;
+        tj = -(d * d) * q;
+        rows.each(c, lane, [&](int r) { col[r] *= scal; });
+    }
+    __syncwarp();
+    if (lane == 0) { col[c] = beta; tau[c] = tj; }
+    __syncwarp();
+}
+
+// One warp applies reflector j to N columns (c > j: A(:,c) -= tau_j v_j (v_j^T A(:,c)))
+// or, for c < j, records the Gram entry G(c, j) = v_c^T v_j: both need the
+// same inner product s_c = A(j, c) + sum_r v_j(r) A(r, c).
+template <int N, class Rows>
+__device__ __forceinline__ void warp_apply(double *S, int ldS, int j, const Rows &rows, const int (&cols)[4],
+                                           double tj, double *G, int w) {
+    const int lane = threadIdx.x & 31;
+    const double *vj = S + (size_t)j * ldS;
+    double acc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = (q < N && lane == 0) ? S[j + (size_t)cols[q] * ldS] : 0.0;
+    rows.each(j, lane, [&](int r) {
+        const double v = vj[r];
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = fma(v, S[r + (size_t)cols[q] * ldS], acc[q]);
+    });
+    warp_sum_n<N>(acc);
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        const int c = cols[q];
+        if (c > j) {
+            const double f = tj * acc[q];
             double *colc = S + (size_t)c * ldS;
-            double d = 0.0;
-            for (int idx = lane; idx < cnt; idx += 32) {
-                const int r = rows.row(j, idx);
-                d = fma(colj[r], colc[r], d);
-            }
-            d = warp_sum(d) + colc[j];
+            rows.each(j, lane, [&](int r) { colc[r] = fma(-f, vj[r], colc[r]); });
+            if (lane == 0) colc[j] -= f;
+        } else if (lane == 0) {
+            G[c + j * w] = acc[q];
+        }
+    }
+}
+
+// Householder QR of the w columns held in shared memory S (column-major,
+// leading dimension ldS); column j acts on its pivot row j and the rows that
+// `rows` lists.  Column c belongs to warp c % nw.  During step j the owner of
+// column j+1 updates that column first and turns it into the next reflector,
+// while the other warps update their columns, so each step needs a single
+// barrier.  On return: R on and above the pivots, the vectors below them
+// (unit pivot implied), tau[0:w], and the strict upper Gram matrix
+// G(c, j) = v_c^T v_j (ld w) from which the kernel T is built.
+template <class Rows>
+__device__ void householder_block(double *S, int ldS, int w, const Rows &rows, double *tau, double *G) {
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (wid == 0) warp_pivot(S, ldS, 0, rows, tau);
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+        const double tj = tau[j];
+        const int nxt = j + 1;
+        if (nxt < w && nxt % nw == wid) {
+            const int one[4] = {nxt, 0, 0, 0};
+            warp_apply<1>(S, ldS, j, rows, one, tj, G, w);
             __syncwarp();
-            if (c > j) {
-                const double f = tj * d;
-                if (lane == 0) colc[j] -= f;
-                for (int idx = lane; idx < cnt; idx += 32) {
-                    const int r = rows.row(j, idx);
-                    colc[r] = fma(-f, colj[r], colc[r]);
-                }
-            } else if (lane == 0) {
-                z[c] = d;
-            }
+            warp_pivot(S, ldS, nxt, rows, tau);
+        }
+        int cols[4] = {0, 0, 0, 0};
+        int g = 0;
+        for (int c = wid; c < w; c += nw) {
+            if (c == j || c == nxt) continue;
+            cols[g++] = c;
+            if (g == 4) { warp_apply<4>(S, ldS, j, rows, cols, tj, G, w); g = 0; }
+        }
+        if (g == 1) warp_apply<1>(S, ldS, j, rows, cols, tj, G, w);
+        else if (g == 2) warp_apply<2>(S, ldS, j, rows, cols, tj, G, w);
+        else if (g == 3) warp_apply<3>(S, ldS, j, rows, cols, tj, G, w);
+        __syncthreads();
+    }
+}
+
+// The kernel T of Q = I - V T V^T from tau and the strict upper Gram matrix
+// G = striu(V^T V): T^{-1} = striu(G) + diag(1/tau) (the closed form of
+// Section 2.3).  Built bottom-up over block sizes s = 1, 2, 4, ...: for each
+// pair of adjacent diagonal blocks T12 = -T11 G12 T22 (the T assembly of
+// Algorithm 2), so the dependency depth is log2(w) small products instead of
+// a w-step recurrence.  M is w x w scratch.  T, G, M: ld w, shared memory.
+__device__ void build_t(double *T, const double *G, const double *tau, double *M, int w) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < w * w; idx += nthr) {
+        const int i = idx % w, c = idx / w;
+        T[idx] = (i == c) ? tau[i] : 0.0;
+    }
+    __syncthreads();
+    for (int s = 1; s < w; s *= 2) {
+        const int s2 = 2 * s;
+        for (int idx = tid; idx < w * w; idx += nthr) {
+            const int row = idx % w, col = idx / w;
+            const int b1 = (row / s2) * s2 + s;
+            if (row >= b1 || col < b1 || col >= b1 + s) continue;
+            double acc = 0.0;   // (G12 T22)(row, col)
+            for (int l = b1; l <= col; ++l) acc = fma(G[row + l * w], T[l + col * w], acc);
+            M[idx] = acc;
         }
         __syncthreads();
-        for (int i = tid; i <= j; i += nthr) {
-            double tv = tj;
-            if (i < j) {
-                double s = 0.0;
-                for (int l = i; l < j; ++l) s = fma(T[i + l * w], z[l], s);
-                tv = -tj * s;
-            }
-            T[i + j * w] = tv;
+        for (int idx = tid; idx < w * w; idx += nthr) {
+            const int row = idx % w, col = idx / w;
+            const int b1 = (row / s2) * s2 + s;
+            if (row >= b1 || col < b1 || col >= b1 + s) continue;
+            double acc = 0.0;   // (T11 M)(row, col)
+            for (int l = row; l < b1; ++l) acc = fma(T[row + l * w], M[l + col * w], acc);
+            T[idx] = -acc;
         }
         __syncthreads();
     }
 }
 
+// Up kernel shared memory: S (ldS x w), then T, G (w x w each), tau (w).
 __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
     extern __shared__ double smem[];
     const int w = p.w, ldS = p.ldS, tid = threadIdx.x, nthr = blockDim.x;
     double *S = smem;
     double *T = S + (size_t)ldS * w;
-    double *tau = T + w * w;
-    double *z = tau + w;
-    double *red = z + w;
+    double *G = T + w * w;
+    double *tau = G + w * w;
     __shared__ int s_last;
 
     const int leaf = blockIdx.x;
@@ -167,18 +245,24 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
     for (int c = 0; c < w; ++c)
         for (int r = tid; r < h; r += nthr) S[(size_t)c * ldS + r] = p.A[(r0 + r) + c * p.lda];
     __syncthreads();
-    householder_block(S, ldS, w, LeafRows{h}, tau, T, red, z);
+    householder_block(S, ldS, w, LeafRows{h}, tau, G);
 
-    // V_p (strict lower) and R_p (upper) back to the panel rows; T_p, R_p to the tree.
+    // V_p (strict lower) and R_p (upper) back to the panel rows, R_p to the tree;
+    // then T_p, with the leaf block's shared memory as scratch.
     for (int c = 0; c < w; ++c)
         for (int r = tid; r < h; r += nthr) p.A[(r0 + r) + c * p.lda] = S[(size_t)c * ldS + r];
     {
-        double *Rn = p.wsR + (size_t)leaf * ww, *Tn = p.wsT + (size_t)leaf * ww;
+        double *Rn = p.wsR + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int i = idx % w, c = idx / w;
             Rn[idx] = (i <= c) ? S[(size_t)c * ldS + i] : 0.0;
-            Tn[idx] = T[idx];
         }
+    }
+    __syncthreads();
+    build_t(T, G, tau, S, w);
+    {
+        double *Tn = p.wsT + (size_t)leaf * ww;
+        for (int idx = tid; idx < w * w; idx += nthr) Tn[idx] = T[idx];
     }
 
     // Climb: the last of a node's children to arrive merges them.
@@ -206,19 +290,21 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
                     S[(size_t)(idx / w) * ldS + i * w + (idx % w)] = __ldcg(Rc + idx);
             }
             __syncthreads();
-            householder_block(S, ldS, w, MergeRows{w, cnt}, tau, T, red, z);
+            householder_block(S, ldS, w, MergeRows{w, cnt}, tau, G);
             double *Rn = p.wsR + (size_t)pidx * ww, *Tn = p.wsT + (size_t)pidx * ww;
             double *Yn = p.wsY + (size_t)(pidx - p.P) * (p.k - 1) * ww;
             for (int idx = tid; idx < w * w; idx += nthr) {
                 const int i = idx % w, c = idx / w;
                 Rn[idx] = (i <= c) ? S[(size_t)c * ldS + i] : 0.0;
-                Tn[idx] = T[idx];
             }
             for (int b = 1; b < cnt; ++b)
                 for (int idx = tid; idx < w * w; idx += nthr) {
                     const int i = idx % w, c = idx / w;
                     Yn[(size_t)(b - 1) * ww + idx] = (i <= c) ? S[(size_t)c * ldS + b * w + i] : 0.0;
                 }
+            __syncthreads();
+            build_t(T, G, tau, S, w);
+            for (int idx = tid; idx < w * w; idx += nthr) Tn[idx] = T[idx];
         } else {
             // single child: the node is the identity, its R passes through
             const double *Rc = p.wsR + (size_t)(off + node) * ww;
@@ -232,30 +318,34 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
     }
 }
 
-// C = Tri * B for w x w matrices in shared memory (ld w); Tri upper triangular.
-__device__ void upper_times(const double *Tri, const double *B, double *C, int w, double sign) {
+// C = sign * A * B for upper triangular w x w A, B (ld w): C is upper
+// triangular, its strict lower part is written as zero.
+__device__ void upper_upper(const double *A, const double *B, double *C, int w, double sign) {
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         const int i = idx % w, c = idx / w;
         double s = 0.0;
-        for (int l = i; l < w; ++l) s = fma(Tri[i + l * w], B[l + c * w], s);
+        for (int l = i; l <= c; ++l) s = fma(A[i + l * w], B[l + c * w], s);
         C[idx] = sign * s;
     }
 }
 
+// Downsweep.  Starting from B = I at the root, each node on the path gives
+// its child [B_0; B_1; ...] = (I - V T V^T)[B; 0] = [B - T B; -Y_1 T B; ...].
+// T, Y and I are upper triangular, so every B stays upper triangular and each
+// product costs about w^3/6 multiply-adds.
 __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
     extern __shared__ double smem[];
     const int w = p.w, ldS = p.ldW, tid = threadIdx.x, nthr = blockDim.x;
     const size_t ww = (size_t)w * w;
     double *B = smem;
     double *C = B + ww;
-    double *M = C + ww;      // node T, then node Y / leaf T_p
+    double *M = C + ww;      // node T / Y, then leaf T_p and products
     double *Vs = M + ww;     // leaf block, ldS x w
 
     const int leaf = blockIdx.x;
     const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
     const int h = (int)(r1 - r0);
 
-    // ancestors and level sizes (L <= 40)
     int anc[41], Nlev[41];
     int64_t offl[41];
     anc[0] = leaf; Nlev[0] = p.P; offl[0] = 0;
@@ -275,7 +365,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
         const double *Tn = p.wsT + (size_t)pidx * ww;
         for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tn[idx];
         __syncthreads();
-        upper_times(M, B, C, w, 1.0);          // C = T_node B
+        upper_upper(M, B, C, w, 1.0);          // C = T_node B
         __syncthreads();
         if (pos == 0) {
             for (int idx = tid; idx < w * w; idx += nthr) B[idx] -= C[idx];
@@ -283,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
             const double *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos - 1)) * ww;
             for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Yn[idx];
             __syncthreads();
-            upper_times(M, C, B, w, -1.0);     // B = -Y_pos C
+            upper_upper(M, C, B, w, -1.0);     // B = -Y_pos C
         }
         __syncthreads();
     }
@@ -296,23 +386,25 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
         for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tp[idx];
     }
     __syncthreads();
-    // C = V1^T B, V1 = unit lower top w x w of the leaf block
+    // C = V1^T B, V1 = unit lower top w x w of the leaf block; B upper -> C upper
     for (int idx = tid; idx < w * w; idx += nthr) {
         const int i = idx % w, c = idx / w;
-        double s = B[i + c * w];
-        for (int l = i + 1; l < w; ++l) s = fma(Vs[(size_t)i * ldS + l], B[l + c * w], s);
+        double s = 0.0;
+        if (i <= c) {
+            s = B[i + c * w];
+            for (int l = i + 1; l <= c; ++l) s = fma(Vs[(size_t)i * ldS + l], B[l + c * w], s);
+        }
         C[idx] = s;
     }
     __syncthreads();
-    // B stays; reuse M <- T_p C  (need a temp: write into Vs? no - use C2 in place of T)
     {
-        // compute Z2 = T_p * C into registers then overwrite M after a barrier
+        // Z = T_p C into registers, then over M after a barrier
         double z2[(kMaxPanel * kMaxPanel + kThreads - 1) / kThreads];
         int q = 0;
         for (int idx = tid; idx < w * w; idx += nthr, ++q) {
             const int i = idx % w, c = idx / w;
             double s = 0.0;
-            for (int l = i; l < w; ++l) s = fma(M[i + l * w], C[l + c * w], s);
+            for (int l = i; l <= c; ++l) s = fma(M[i + l * w], C[l + c * w], s);
             z2[q] = s;
         }
         __syncthreads();
@@ -320,18 +412,48 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
         for (int idx = tid; idx < w * w; idx += nthr, ++q) M[idx] = z2[q];
     }
     __syncthreads();
-    // W(r, c) = [B; 0](r, c) - sum_{i <= min(r, w-1)} Vhat(r, i) Z2(i, c)
+    // W(r, c) = [B; 0](r, c) - sum_{i <= min(r, c)} Vhat(r, i) Z(i, c), Z upper
     for (int idx = tid; idx < h * w; idx += nthr) {
         const int r = idx % h, c = idx / h;
+        const int iend = min(r, c + 1);
         double s = 0.0;
-        const int imax = min(r, w - 1);
-        for (int i = 0; i < imax; ++i) s = fma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
-        // i == imax: unit diagonal if r < w, stored entry otherwise
-        s += (r < w ? 1.0 : Vs[(size_t)imax * ldS + r]) * M[imax + c * w];
-        const double bw = (r < w) ? B[r + c * w] : 0.0;
-        const double wv = bw - s;
+        for (int i = 0; i < iend; ++i) s = fma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
+        if (r <= c) s += M[r + c * w];
+        const double wv = ((r < w) ? B[r + c * w] : 0.0) - s;
         p.A[(r0 + r) + c * p.lda] = wv;
         if (leaf == 0 && r < w) p.wsX[r + c * w] = wv;
+    }
+}
+
+// Inverse of the unit lower triangular L (ld w) into Li (ld w), blocked
+// bottom-up like build_t: Li21 = -Li22 L21 Li11 for each pair of blocks.
+__device__ void unit_lower_inverse(const double *L, double *Li, double *M, int w) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < w * w; idx += nthr) {
+        const int i = idx % w, c = idx / w;
+        Li[idx] = (i == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int s = 1; s < w; s *= 2) {
+        const int s2 = 2 * s;
+        for (int idx = tid; idx < w * w; idx += nthr) {
+            const int row = idx % w, col = idx / w;
+            const int b1 = (col / s2) * s2 + s;   // pair (b0 = b1 - s, b1), col in block 0, row in block 1
+            if (col >= b1 || row < b1 || row >= b1 + s) continue;
+            double acc = 0.0;   // (L21 Li11)(row, col)
+            for (int l = col; l < b1; ++l) acc = fma(L[row + l * w], Li[l + col * w], acc);
+            M[idx] = acc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < w * w; idx += nthr) {
+            const int row = idx % w, col = idx / w;
+            const int b1 = (col / s2) * s2 + s;
+            if (col >= b1 || row < b1 || row >= b1 + s) continue;
+            double acc = M[idx];   // Li22(row,row) = 1
+            for (int l = b1; l < row; ++l) acc = fma(Li[row + l * w], M[l + col * w], acc);
+            Li[idx] = -acc;
+        }
+        __syncthreads();
     }
 }
 
@@ -341,7 +463,9 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
     const size_t ww = (size_t)w * w;
     double *X = smem;            // w x w: L (strict lower) and U (upper)
     double *Tm = X + ww;         // w x w
-    double *Sg = Tm + ww;        // w signs
+    double *Li = Tm + ww;        // w x w
+    double *Ms = Li + ww;        // w x w scratch
+    double *Sg = Ms + ww;        // w signs
     double *rU = Sg + w;         // w reciprocals of diag(U)
     double *Wb = rU + w;         // ldS x w
 
@@ -369,16 +493,13 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
 
     const int leaf = blockIdx.x;
     if (leaf == 0) {
-        // T = U S L^{-T}:  T(:, j) = U(:, j) S_j - sum_{l<j} L(j, l) T(:, l); thread i owns row i.
-        for (int i = tid; i < w; i += nthr) {
-            for (int j = 0; j < w; ++j) {
-                double t = 0.0;
-                if (i <= j) {
-                    t = X[i + j * w] * Sg[j];
-                    for (int l = i; l < j; ++l) t = fma(-X[j + l * w], Tm[i + l * w], t);
-                }
-                Tm[i + j * w] = t;
-            }
+        // T = U S L^{-T}: T(i, c) = sum_{l=i}^{c} U(i, l) S_l Li(c, l)
+        unit_lower_inverse(X, Li, Ms, w);
+        for (int idx = tid; idx < w * w; idx += nthr) {
+            const int i = idx % w, c = idx / w;
+            double t = 0.0;
+            for (int l = i; l <= c; ++l) t = fma(X[i + l * w] * Sg[l], (l == c) ? 1.0 : Li[c + l * w], t);
+            Tm[idx] = t;
         }
         __syncthreads();
         for (int idx = tid; idx < w * w; idx += nthr) {
@@ -416,31 +537,34 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
         for (int r = tid; r < h; r += nthr) p.A[(rs + r) + c * p.lda] = Wb[(size_t)c * ldS + r];
 }
 
-size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + (size_t)w * w + 2 * w + 32); }
+size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + w); }
 size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 3 * (size_t)w * w); }
-size_t recon_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + 2 * w); }
+size_t recon_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 4 * (size_t)w * w + 2 * w); }
 
 constexpr size_t kSmemCap = 200 * 1024;
+constexpr int kDefaultFanout = 4;
 
 }  // namespace
 
 bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPlan *plan) {
-    (void)num_sms;
     if (w < 1 || w > kMaxPanel || mp < w) return false;
     TsqrPlan pl;
     pl.mp = mp; pl.w = w;
     // fan-out: as requested, but the merge of k stacked triangles (k*w rows)
     // must fit the up kernel's shared memory
-    int k = std::min(8, std::max(2, fanout > 0 ? fanout : 2));
+    int k = std::min(8, std::max(2, fanout > 0 ? fanout : kDefaultFanout));
     while (k > 2 && up_smem(k * w, w) > kSmemCap) --k;
     pl.k = k;
     // tallest leaf that every kernel's shared memory can hold
     const size_t cap_el = kSmemCap / sizeof(double);
-    int64_t hcap = (int64_t)((cap_el - ((size_t)w * w + 2 * w + 32)) / w);                 // up
+    int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + w)) / w);                      // up
     hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 3 * (size_t)w * w) / w));           // down
-    hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 2 * (size_t)w * w - 2 * w) / w));   // recon
+    hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 4 * (size_t)w * w - 2 * w) / w));   // recon
     if (hcap < w) return false;
-    int64_t target = leaf_rows > 0 ? leaf_rows : std::max<int64_t>(2 * w, 64);
+    // default: about one leaf per SM (the leaf phase is the only one that
+    // uses the whole GPU), never shorter than the panel is wide
+    const int sms = num_sms > 0 ? num_sms : 152;
+    int64_t target = leaf_rows > 0 ? leaf_rows : std::max<int64_t>(w, (mp + sms - 1) / sms);
     target = std::max<int64_t>(target, w);
     int64_t P = (mp + target - 1) / target;
     P = std::max<int64_t>(P, (mp + hcap - 1) / hcap);   // leaves no taller than hcap
@@ -472,17 +596,26 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
 }
 
 TsqrPlan tsqr_plan_bound(int64_t mp, int w, int leaf_rows, int fanout, int num_sms) {
-    // Workspace grows with the number of leaves, which grows with mp and
-    // shrinks with w: take the element-wise maximum over widths 1..w at mp.
+    // Workspace grows with the number of leaves P.  For panels of height
+    // <= mp and width ww <= w: with an explicit leaf height P grows with the
+    // height; with the default (about one leaf per SM) a shorter panel can
+    // round to more leaves, but never to more than the SM count.  Take the
+    // larger of the two counts, then the node counts of a tree that size.
     TsqrPlan best;
+    const int sms = num_sms > 0 ? num_sms : 152;
     for (int ww = 1; ww <= w; ++ww) {
         TsqrPlan pl;
         if (mp < ww || !tsqr_plan(mp, ww, leaf_rows, fanout, num_sms, &pl)) continue;
-        best.nR = std::max(best.nR, pl.nR);
-        best.nT = std::max(best.nT, pl.nT);
-        best.nY = std::max(best.nY, pl.nY);
-        best.nX = std::max(best.nX, pl.nX);
-        best.ncount = std::max(best.ncount, pl.ncount);
+        int64_t P = pl.P;
+        if (leaf_rows <= 0) P = std::max<int64_t>(P, std::min<int64_t>(sms, mp / ww));
+        int64_t nodes = P, Nl = P, internal = 0;
+        while (Nl > 1) { Nl = (Nl + pl.k - 1) / pl.k; nodes += Nl; internal += Nl; }
+        const size_t w2 = (size_t)ww * ww;
+        best.nR = std::max(best.nR, (size_t)nodes * w2);
+        best.nT = std::max(best.nT, (size_t)nodes * w2);
+        best.nY = std::max(best.nY, (size_t)std::max<int64_t>(internal, 1) * (pl.k - 1) * w2);
+        best.nX = std::max(best.nX, w2);
+        best.ncount = std::max(best.ncount, (size_t)std::max<int64_t>(internal, 1));
     }
     return best;
 }

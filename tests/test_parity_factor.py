@@ -170,3 +170,14 @@ def test_host_pointers(gb, ctx, orc):
                         t.ctypes.data_as(ctypes.c_void_p), 50, gb.GBQR_T_FULL, None)
     assert st == gb.GBQR_OK
     _gpu.compare_factor(a, vr, t, gb.GBQR_T_FULL, 50, orc, "host pointers")
+
+
+@pytest.mark.parametrize("lookahead", [0, -1])
+@pytest.mark.parametrize("m,n,nb", [(2000, 300, 16), (640, 640, 64), (5000, 129, 32)])
+def test_lookahead_on_and_off(gb, ctx, orc, m, n, nb, lookahead):
+    """The look-ahead schedule (panel k+1 on a second stream) reorders work
+    but not arithmetic: both schedules match the oracle."""
+    a = workloads.graded(m, n, 20 + nb)
+    o = gb.opts(panel_nb=nb, lookahead=lookahead)
+    VR, T, nbr = _gpu.factor_gpu(ctx, a, gb.GBQR_T_PANEL, o)
+    _gpu.compare_factor(a, VR, T, gb.GBQR_T_PANEL, nbr, orc, f"lookahead={lookahead} nb={nb}")
