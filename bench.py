@@ -64,6 +64,27 @@ def parse():
     return p.parse_args()
 
 
+# ------------------------------------------------------------- multi-rank
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Each rank factors its own matrix (independent replicas)."""
+    return base_seed + rank
+
+
+def max_over_ranks(value: float, dist, device="cpu") -> float:
+    """The slowest rank's time: all-reduce MAX (the only collective; it is on
+    the timing path, never on the data path)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank: float, world: int, ms_per_step: float) -> float:
+    return flops_per_rank * world / (ms_per_step * 1e-3) / 1e12
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons while running."""
@@ -203,7 +224,8 @@ def run_gbqr(args):
     nb = args.panel or gb.default_panel_nb(w.m, w.n)
     trows = w.n if layout == gb.GBQR_T_FULL else min(nb, w.n)
 
-    a_host = workloads.graded(w.m, w.n, w.seed + rank) if w.graded else workloads.gaussian(w.m, w.n, w.seed + rank)
+    seed = replica_seed(w.seed, rank)
+    a_host = workloads.graded(w.m, w.n, seed) if w.graded else workloads.gaussian(w.m, w.n, seed)
     stream = torch.cuda.current_stream(dev)
     ctx = gb.Context(dev, stream)
     A0 = gb.to_colmajor(a_host, f"cuda:{dev}")
@@ -244,12 +266,8 @@ def run_gbqr(args):
     ctx.trace(False)
     launches = ctx.launch_count() - launches0
     clocks = clk.summary()
-    ms_step = ms_total / args.steps
-    if dist:
-        t = torch.tensor([ms_step], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = w.flops * world / (ms_step * 1e-3) / 1e12
+    ms_step = max_over_ranks(ms_total / args.steps, dist, f"cuda:{dev}")
+    value = whole_job_tflops(w.flops, world, ms_step)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     a_pin = torch.from_numpy(np.ascontiguousarray(a_host.T)).pin_memory()   # (n, m) row-major = A column-major

@@ -82,6 +82,12 @@ struct LeafRows {
     __device__ __forceinline__ void each(int j, int lane, F &&f) const {
         for (int r = j + 1 + lane; r < h; r += 32) f(r);
     }
+    // pivot row j first (f(r, true)), then rows(j): one pass, no separate
+    // pivot-row term
+    template <class F>
+    __device__ __forceinline__ void each_with_pivot(int j, int lane, F &&f) const {
+        for (int r = j + lane; r < h; r += 32) f(r, r == j);
+    }
 };
 
 // Rows of column j below its pivot in cnt stacked w x w upper triangles:
@@ -92,6 +98,15 @@ struct MergeRows {
     __device__ __forceinline__ void each(int j, int lane, F &&f) const {
         for (int i = 1; i < cnt; ++i)
             for (int r = lane; r <= j; r += 32) f(i * w + r);
+    }
+    template <class F>
+    __device__ __forceinline__ void each_with_pivot(int j, int lane, F &&f) const {
+        const int n = 1 + (cnt - 1) * (j + 1);
+        for (int idx = lane; idx < n; idx += 32) {
+            if (idx == 0) { f(j, true); continue; }
+            const int b = (idx - 1) / (j + 1);
+            f((b + 1) * w + (idx - 1 - b * (j + 1)), false);
+        }
     }
 };
 
@@ -132,11 +147,9 @@ __device__ __forceinline__ void warp_apply(double *S, int ldS, int j, const Rows
                                            double tj, double *G, int w) {
     const int lane = threadIdx.x & 31;
     const double *vj = S + (size_t)j * ldS;
-    double acc[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = (q < N && lane == 0) ? S[j + (size_t)cols[q] * ldS] : 0.0;
-    rows.each(j, lane, [&](int r) {
-        const double v = vj[r];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    rows.each_with_pivot(j, lane, [&](int r, bool piv) {
+        const double v = piv ? 1.0 : vj[r];
 #pragma unroll
         for (int q = 0; q < N; ++q) acc[q] = fma(v, S[r + (size_t)cols[q] * ldS], acc[q]);
     });
@@ -147,8 +160,9 @@ __device__ __forceinline__ void warp_apply(double *S, int ldS, int j, const Rows
         if (c > j) {
             const double f = tj * acc[q];
             double *colc = S + (size_t)c * ldS;
-            rows.each(j, lane, [&](int r) { colc[r] = fma(-f, vj[r], colc[r]); });
-            if (lane == 0) colc[j] -= f;
+            rows.each_with_pivot(j, lane, [&](int r, bool piv) {
+                colc[r] = fma(-f, piv ? 1.0 : vj[r], colc[r]);
+            });
         } else if (lane == 0) {
             G[c + j * w] = acc[q];
         }
@@ -157,10 +171,13 @@ __device__ __forceinline__ void warp_apply(double *S, int ldS, int j, const Rows
 
 // Householder QR of the w columns held in shared memory S (column-major,
 // leading dimension ldS); column j acts on its pivot row j and the rows that
-// `rows` lists.  Column c belongs to warp c % nw.  During step j the owner of
-// column j+1 updates that column first and turns it into the next reflector,
-// while the other warps update their columns, so each step needs a single
-// barrier.  On return: R on and above the pivots, the vectors below them
+// `rows` lists.  During step j one warp (j % nw) updates column j+1 and turns
+// it into the next reflector while the other warps share every remaining
+// column round robin, so each step needs a single barrier.  On GB300 a warp
+// issues at most one FP64 instruction per ~64 cycles and an SM sub-partition
+// one per ~76, so the step time is the FP64 instruction count of the busiest
+// warp / sub-partition: the pivot warp (square root, reciprocal, one warp
+// reduction) carries nothing else.  On return: R on and above the pivots, the vectors below them
 // (unit pivot implied), tau[0:w], and the strict upper Gram matrix
 // G(c, j) = v_c^T v_j (ld w) from which the kernel T is built.
 template <class Rows>
@@ -171,22 +188,29 @@ __device__ void householder_block(double *S, int ldS, int w, const Rows &rows, d
     for (int j = 0; j < w; ++j) {
         const double tj = tau[j];
         const int nxt = j + 1;
-        if (nxt < w && nxt % nw == wid) {
-            const int one[4] = {nxt, 0, 0, 0};
-            warp_apply<1>(S, ldS, j, rows, one, tj, G, w);
-            __syncwarp();
-            warp_pivot(S, ldS, nxt, rows, tau);
+        const int pw = j % nw;                         // pivot warp of this step
+        if (wid == pw) {
+            if (nxt < w) {
+                const int one[4] = {nxt, 0, 0, 0};
+                warp_apply<1>(S, ldS, j, rows, one, tj, G, w);
+                __syncwarp();
+                warp_pivot(S, ldS, nxt, rows, tau);
+            }
+        } else {
+            // every other column (not j, not j+1) to the other warps, round robin
+            const int nexcl = (nxt < w) ? 2 : 1;
+            const int ncols = w - nexcl;
+            const int me = (wid - pw - 1 + nw) % nw;  // 0 .. nw-2
+            int cols[4] = {0, 0, 0, 0};
+            int g = 0;
+            for (int t = me; t < ncols; t += nw - 1) {
+                cols[g++] = (t < j) ? t : t + nexcl;
+                if (g == 4) { warp_apply<4>(S, ldS, j, rows, cols, tj, G, w); g = 0; }
+            }
+            if (g == 1) warp_apply<1>(S, ldS, j, rows, cols, tj, G, w);
+            else if (g == 2) warp_apply<2>(S, ldS, j, rows, cols, tj, G, w);
+            else if (g == 3) warp_apply<3>(S, ldS, j, rows, cols, tj, G, w);
         }
-        int cols[4] = {0, 0, 0, 0};
-        int g = 0;
-        for (int c = wid; c < w; c += nw) {
-            if (c == j || c == nxt) continue;
-            cols[g++] = c;
-            if (g == 4) { warp_apply<4>(S, ldS, j, rows, cols, tj, G, w); g = 0; }
-        }
-        if (g == 1) warp_apply<1>(S, ldS, j, rows, cols, tj, G, w);
-        else if (g == 2) warp_apply<2>(S, ldS, j, rows, cols, tj, G, w);
-        else if (g == 3) warp_apply<3>(S, ldS, j, rows, cols, tj, G, w);
         __syncthreads();
     }
 }
@@ -542,7 +566,7 @@ size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 3 
 size_t recon_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 4 * (size_t)w * w + 2 * w); }
 
 constexpr size_t kSmemCap = 200 * 1024;
-constexpr int kDefaultFanout = 4;
+constexpr int kDefaultFanout = 8;
 
 }  // namespace
 
