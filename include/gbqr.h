@@ -105,7 +105,7 @@ typedef struct {
 
 /* Per-kernel-family totals of traced launches (see gbqr_trace_enable). */
 typedef struct {
-    char name[24];         /* "gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other" */
+    char name[24];         /* "gemm", "tc_gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other" */
     int64_t launches;
     double ms;             /* summed device time between launch-bracketing events */
     double flops;          /* summed algorithmic FP64 flops of those launches */
@@ -199,6 +199,25 @@ GBQR_API gbqr_status gbqr_form_q(gbqr_ctx *ctx, int64_t m, int64_t n, const doub
 GBQR_API gbqr_status gbqr_ls_solve(gbqr_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
                           const double *b, double *x, int prec, gbqr_info *info);
 
+/* ---- tensor-core GEMM (mixed precision building block) ----------------- */
+
+/* C = alpha * op(A) * B + beta * C for FP64 column-major matrices, computed
+ * on the tcgen05 tensor cores: each operand is split into nsplit (1..3) BF16
+ * slices x = x_1 + ... (x_1 = bf16(x), x_2 = bf16(x - x_1), ...) and the
+ * slice products x_i y_j with i + j <= nsplit + 1 are accumulated in FP32
+ * (1, 3 or 6 products).  op(A) = A^T (A stored K x M) when transa != 0, else
+ * A (stored M x K); B is stored K x N; C is M x N.  This is the product the
+ * mixed-precision path uses for the update M1 = V^T A_R, A_R -= V M2 of
+ * Algorithm 2 / the right-looking update (Section 8.4) in place of FP64.
+ * Accuracy: about 2^-8, 2^-16, 2^-23 relative to |A||B| for nsplit 1, 2, 3
+ * (FP32 accumulation over K adds ~K 2^-24).  Operand magnitudes must stay
+ * within BF16's exponent range (|x| < 3e38; slices below ~1e-38 flush).
+ * Asynchronous; needs workspace for the slices (grown automatically).
+ * Errors: EINVAL, ENOMEM, ECUDA; a device-side timeout shows at gbqr_sync. */
+GBQR_API gbqr_status gbqr_gemm_split_bf16(gbqr_ctx *ctx, int transa, int64_t M, int64_t N, int64_t K,
+                                          double alpha, const double *A, int64_t lda, const double *B,
+                                          int64_t ldb, double beta, double *C, int64_t ldc, int nsplit);
+
 /* ---- tracing ------------------------------------------------------------ */
 
 /* Turn launch tracing on (non-zero) or off.  While on, every kernel launch is
@@ -253,6 +272,13 @@ GBQR_API gbqr_status gbqr_tsqr_static(int64_t m, int64_t n, double *A, int64_t l
  * that the FP64 kernels are reported against.  Synchronous; allocates 8
  * bytes.  Errors: EINVAL, ENOMEM, ECUDA. */
 GBQR_API gbqr_status gbqr_fp64_peak(int device, int kind, int iters, double *tflops);
+
+/* Cycles per dependent FP64 operation of a warp when `warps` warps (1..32)
+ * of one CTA run such chains at once: op 0 = FMA, 1 = sqrt, 2 = reciprocal
+ * (each with an add).  The paper has no counterpart: it measures the issue
+ * cost that bounds the latency-bound steps (reflector generation).
+ * Synchronous; allocates 8.3 KB.  Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_fp64_issue_cycles(int device, int op, int warps, double *cycles);
 
 /* Human-readable name of a status. */
 GBQR_API const char *gbqr_strerror(gbqr_status s);

@@ -62,11 +62,14 @@ SIGNATURES = {
     "gbqr_apply_q": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _I64, _P, _I64]),
     "gbqr_form_q": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _P, _I64]),
     "gbqr_ls_solve": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _P, ctypes.c_int, ctypes.POINTER(gbqr_info)]),
+    "gbqr_gemm_split_bf16": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, ctypes.c_double, _P, _I64, _P, _I64,
+                                             ctypes.c_double, _P, _I64, ctypes.c_int]),
     "gbqr_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gbqr_trace_read": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_trace_rec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_launch_count": (_I64, [_P]),
     "gbqr_tsqr_static": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
     "gbqr_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "gbqr_fp64_issue_cycles": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gbqr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 
@@ -249,6 +252,16 @@ class Context:
         return check(gbqr_form_q(self.handle, m, n, _P(pv), lda, _P(pt), ldt, layout, nb, _P(pq), ldq),  # noqa: F821
                      "gbqr_form_q")
 
+    def gemm_split_bf16(self, A, B, C, transa: bool = False, alpha: float = 1.0, beta: float = 0.0,
+                        nsplit: int = 3) -> int:
+        """C = alpha op(A) B + beta C on the tensor cores (split-BF16)."""
+        pa, ra, ca, lda = _cm(A, "A")
+        pb, kb, nb_, ldb = _cm(B, "B")
+        pc, mc, nc, ldc = _cm(C, "C")
+        M, K = (ca, ra) if transa else (ra, ca)
+        return check(gbqr_gemm_split_bf16(self.handle, 1 if transa else 0, M, nc, K, alpha, _P(pa), lda,  # noqa: F821
+                                          _P(pb), ldb, beta, _P(pc), ldc, nsplit), "gbqr_gemm_split_bf16")
+
     def ls_solve(self, A, b, x, prec: int = GBQR_FP64):
         pa, m, n, lda = _cm(A, "A")
         info = gbqr_info()
@@ -267,6 +280,14 @@ def fp64_peak(device: int = 0, kind: int = 0, iters: int = 20000) -> float:
     load()
     out = ctypes.c_double(0.0)
     check(gbqr_fp64_peak(device, kind, iters, ctypes.byref(out)), "gbqr_fp64_peak")  # noqa: F821
+    return out.value
+
+
+def fp64_issue_cycles(device: int = 0, op: int = 0, warps: int = 1) -> float:
+    """Cycles per dependent FP64 op per warp (op 0 FMA, 1 sqrt, 2 reciprocal)."""
+    load()
+    out = ctypes.c_double(0.0)
+    check(gbqr_fp64_issue_cycles(device, op, warps, ctypes.byref(out)), "gbqr_fp64_issue_cycles")  # noqa: F821
     return out.value
 
 

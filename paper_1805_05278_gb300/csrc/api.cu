@@ -26,6 +26,8 @@ constexpr int64_t kDefaultPanel = 128;
 struct DeviceInfo {
     unsigned long long nonfinite;
     long long rankdef;
+    int timeout;       // a bounded device-side wait ran out
+    int pad;
 };
 
 // ------------------------------------------------------------ event tracer
@@ -59,7 +61,7 @@ struct EventTracer final : Tracer {
     }
 };
 
-const char *kFamilyNames[FAM_COUNT] = {"gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other"};
+const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other"};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -468,7 +470,7 @@ gbqr_status gbqr_create(gbqr_ctx **out, int device, void *cuda_stream) {
         return GBQR_ECUDA;
     }
     if (cudaMalloc((void **)&cx->dinfo, sizeof(DeviceInfo)) != cudaSuccess) { delete cx; return GBQR_ENOMEM; }
-    DeviceInfo zero{0ull, LLONG_MAX};
+    DeviceInfo zero{0ull, LLONG_MAX, 0, 0};
     if (cudaMemcpy(cx->dinfo, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaFree(cx->dinfo);
         delete cx;
@@ -544,15 +546,16 @@ gbqr_status gbqr_sync(gbqr_ctx *cx, gbqr_info *info) {
     if (!cx) return GBQR_EINVAL;
     if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
     if (cudaStreamSynchronize(cx->stream) != cudaSuccess) return GBQR_ECUDA;
-    DeviceInfo h{0ull, LLONG_MAX};
+    DeviceInfo h{0ull, LLONG_MAX, 0, 0};
     if (cudaMemcpy(&h, cx->dinfo, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) return GBQR_ECUDA;
-    DeviceInfo zero{0ull, LLONG_MAX};
+    DeviceInfo zero{0ull, LLONG_MAX, 0, 0};
     if (cudaMemcpy(cx->dinfo, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) return GBQR_ECUDA;
     if (info) {
         memset(info, 0, sizeof *info);
         info->nonfinite = (int64_t)h.nonfinite;
         info->rankdef_col = h.rankdef == LLONG_MAX ? -1 : (int64_t)h.rankdef;
     }
+    if (h.timeout) return GBQR_ETIMEOUT;
     return h.nonfinite ? GBQR_ENONFINITE : GBQR_OK;
 }
 
@@ -696,5 +699,39 @@ gbqr_status gbqr_trace_read(gbqr_ctx *cx, gbqr_trace_rec *out, int max, int *cou
 }
 
 int64_t gbqr_launch_count(const gbqr_ctx *cx) { return cx ? cx->launches : 0; }
+
+gbqr_status gbqr_gemm_split_bf16(gbqr_ctx *cx, int transa, int64_t M, int64_t N, int64_t K, double alpha,
+                                 const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                                 double *C, int64_t ldc, int nsplit) {
+    if (!cx) return GBQR_EINVAL;
+    if (M < 0 || N < 0 || K < 0 || nsplit < 1 || nsplit > 3) return GBQR_EINVAL;
+    if (lda < std::max<int64_t>(1, transa ? K : M) || ldb < std::max<int64_t>(1, K) || ldc < std::max<int64_t>(1, M))
+        return GBQR_EINVAL;
+    if (M == 0 || N == 0) return GBQR_OK;
+    if (!A || !B || !C) return GBQR_EINVAL;
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    const size_t need = tc_gemm_scratch_bytes(M, N, std::max<int64_t>(K, 1), cx->num_sms);
+    TRY(ensure_workspace(cx, need));
+    Exec ex = cx->exec();
+    TcGemmOp op;
+    op.M = M; op.N = N; op.K = K;
+    op.A = A; op.lda = lda; op.ta = transa != 0;
+    op.B = B; op.ldb = ldb;
+    op.C = C; op.ldc = ldc; op.alpha = alpha; op.beta = beta;
+    op.nsplit = nsplit;
+    TcScratch sc;
+    sc.base = cx->ws;
+    sc.bytes = cx->ws_bytes;
+    sc.err = &cx->dinfo->timeout;
+    if (K == 0) {
+        // C = beta * C: one FP64 GEMM launch with an empty K range does exactly that
+        GemmOp g;
+        g.M = M; g.N = N; g.K = 0; g.A = A; g.lda = lda; g.B = B; g.ldb = 1; g.C = C; g.ldc = ldc;
+        g.alpha = alpha; g.beta = beta;
+        GemmScratch gs;
+        return gemm(ex, g, gs);
+    }
+    return tc_gemm(ex, op, sc);
+}
 
 }  // extern "C"

@@ -14,7 +14,7 @@ constexpr int kThreads = 256;   // threads per CTA for every kernel family
 constexpr int kMaxPanel = 64;   // largest TSQR panel width w (= cutoff b)
 
 // ---------------------------------------------------------------- tracing
-enum Family { FAM_GEMM = 0, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TSQR_RECON, FAM_OTHER, FAM_COUNT };
+enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TSQR_RECON, FAM_OTHER, FAM_COUNT };
 
 struct Tracer {
     virtual void begin(cudaStream_t s, Family f) = 0;
@@ -72,6 +72,28 @@ size_t gemm_counters_max(int num_sms);
 gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc);
 // Algorithmic flops of op (structural zeros of masked operands excluded).
 double gemm_algorithmic_flops(const GemmOp &op);
+
+#define TRY_ST(x) do { gbqr_status _s = (x); if (_s != GBQR_OK) return _s; } while (0)
+
+// ------------------------------------------------------ tensor-core GEMM
+// C (FP64, M x N) = alpha * op(A) * B + beta * C with op(A) = A^T when ta
+// (A stored K x M) or A (stored M x K), B stored K x N, on tcgen05 tensor
+// cores as the sum of BF16 slice products (nsplit slices per operand, FP32
+// accumulation).  Masks as for gemm().
+struct TcGemmOp {
+    int64_t M = 0, N = 0, K = 0;
+    const double *A = nullptr; int64_t lda = 1; bool ta = false; int maskA = MASK_NONE;
+    const double *B = nullptr; int64_t ldb = 1; int maskB = MASK_NONE;
+    double *C = nullptr; int64_t ldc = 1;
+    double alpha = 1.0, beta = 0.0;
+    int nsplit = 3;
+};
+struct TcScratch {
+    void *base = nullptr; size_t bytes = 0;   // slices + split-K partials
+    int *err = nullptr;                       // device flag raised on a timed-out wait
+};
+size_t tc_gemm_scratch_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
+gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc);
 
 // ------------------------------------------------------------------ TSQR
 // Base case of Algorithm 2: TSQR of an mp x w panel (Section 5, Appendix C).

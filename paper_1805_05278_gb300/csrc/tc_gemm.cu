@@ -1,0 +1,445 @@
+// Split-BF16 GEMM on the 5th-generation tensor cores (tcgen05), for the
+// mixed-precision form of the update products of QR (Algorithm 2 and the
+// right-looking update of Section 8.4):
+//
+//   C (FP64, M x N) = alpha * op(A) * B + beta * C,   op(A) = A or A^T,
+//
+// with each FP64 operand split into s <= 3 BF16 slices x = x_1 + x_2 + x_3
+// (x_1 = bf16(x), x_2 = bf16(x - x_1), ...), and the products x_i y_j with
+// i + j <= s + 1 (6 products for s = 3) accumulated in FP32 in tensor memory:
+// FP32-level accuracy from BF16 tensor cores.
+//
+// Kernel structure (one CTA per 128 x BN output tile, 6 warps):
+//   warp 0      TMA producer: 3-D tensor loads (K x rows x slice) of 128 x 64
+//               BF16 tiles, 128-byte swizzle, into a 4-stage ring guarded by
+//               mbarriers (full: bytes landed; empty: MMAs done reading).
+//   warp 1      allocates TMEM; one thread issues tcgen05.mma kind::f16
+//               (M = 128, N = BN, K = 16 per instruction) and tcgen05.commit.
+//   warps 2-5   epilogue: tcgen05.ld the FP32 accumulator (warp w reads TMEM
+//               lanes 32*(w%4) .. +31), combine into C in FP64 (or write FP32
+//               split-K partials).
+// Every mbarrier wait is bounded (about 2 s by %globaltimer); on timeout the
+// kernel raises an error flag, stops issuing work, drains what it issued and
+// frees its TMEM.
+#include "common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace gbqr {
+namespace {
+
+constexpr int TC_BM = 128;
+constexpr int TC_BK = 64;          // one 128-byte swizzle row of BF16
+constexpr int TC_STAGES = 4;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t A_TILE_BYTES = TC_BM * TC_BK * 2;
+
+struct TcParams {
+    int M, N, K;
+    int ktiles_per_split;
+    int npairs;
+    int pair_a[6], pair_b[6];
+    double *C; int64_t ldc;
+    double alpha, beta;
+    float *partial;          // split-K partials: [z][M x N] column-major
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase of the given parity; give up after ~2 s or as soon as
+// another thread of the grid has raised the error flag.
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, int *err) {
+    if (mbar_try(a, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try(a, parity)) return true;
+        if (*(volatile int *)err) return false;
+        if (global_ns() - t0 > 2000000000ull) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major BF16 tile written by TMA with
+// 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);   // start address
+    d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                   // descriptor version
+    d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    constexpr uint32_t B_TILE_BYTES = BN * TC_BK * 2;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = sA + TC_STAGES * A_TILE_BYTES;
+    uint64_t *bars = (uint64_t *)(sB + TC_STAGES * B_TILE_BYTES);   // full[S], empty[S], done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * TC_STAGES + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN, z = blockIdx.z;
+    const int ktiles = (p.K + TC_BK - 1) / TC_BK;
+    const int kt0 = z * p.ktiles_per_split;
+    const int nk = max(0, min(ktiles, kt0 + p.ktiles_per_split) - kt0);
+    const int total = nk * p.npairs;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < total; ++it) {
+                const int s = it % TC_STAGES, r = it / TC_STAGES;
+                if (!mbar_wait(empty0 + 8 * s, (uint32_t)((r & 1) ^ 1), p.err)) break;
+                const int pair = it / nk, kt = kt0 + it % nk;
+                mbar_expect_tx(full0 + 8 * s, A_TILE_BYTES + B_TILE_BYTES);
+                tma_load_3d(smem_u32(sA + s * A_TILE_BYTES), &tmA, kt * TC_BK, m0, p.pair_a[pair], full0 + 8 * s);
+                tma_load_3d(smem_u32(sB + s * B_TILE_BYTES), &tmB, kt * TC_BK, n0, p.pair_b[pair], full0 + 8 * s);
+                issued = it + 1;
+            }
+            // after an abort, let the loads already issued land before the CTA exits
+            if (issued < total)
+                for (int it = max(0, issued - TC_STAGES); it < issued; ++it)
+                    mbar_wait(full0 + 8 * (it % TC_STAGES), (uint32_t)((it / TC_STAGES) & 1), p.err);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(TC_BM, BN);
+            for (int it = 0; it < total; ++it) {
+                const int s = it % TC_STAGES, r = it / TC_STAGES;
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)(r & 1), p.err)) break;
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(smem_u32(sA + s * A_TILE_BYTES));
+                const uint64_t bd = sw128_desc(smem_u32(sB + s * B_TILE_BYTES));
+#pragma unroll
+                for (int kk = 0; kk < TC_BK / 16; ++kk)
+                    mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(done);   // arrives once every MMA issued above has completed
+        }
+    } else {
+        const int q = warp & 3;             // TMEM lane quadrant of this warp
+        const int row = q * 32 + lane;
+        const bool ok = mbar_wait(done, 0u, p.err);
+        tc_fence_after();
+        const int m = m0 + row;
+#pragma unroll 1
+        for (int chunk = 0; chunk < BN / 32; ++chunk) {
+            uint32_t v[32];
+            if (total > 0) tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(chunk * 32), v);
+            if (!ok || m >= p.M) continue;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int n = n0 + chunk * 32 + c;
+                if (n >= p.N) break;
+                const float d = (total > 0) ? __uint_as_float(v[c]) : 0.0f;
+                if (p.partial) {
+                    p.partial[(size_t)z * p.M * p.N + m + (size_t)n * p.M] = d;
+                } else {
+                    double *cp = p.C + m + (size_t)n * p.ldc;
+                    double out = p.alpha * (double)d;
+                    if (p.beta != 0.0) out = fma(p.beta, *cp, out);
+                    *cp = out;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    }
+}
+
+// C = beta * C + alpha * sum_z P[z] (FP64 accumulation of FP32 partials).
+__global__ void __launch_bounds__(kThreads) tc_reduce_kernel(int M, int N, int S, const float *P, double *C,
+                                                           int64_t ldc, double alpha, double beta) {
+    const int64_t total = (int64_t)M * N;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < S; ++z) s += (double)P[(size_t)z * total + e];
+        const int64_t m = e % M, n = e / M;
+        double *cp = C + m + n * ldc;
+        double out = alpha * s;
+        if (beta != 0.0) out = fma(beta, *cp, out);
+        *cp = out;
+    }
+}
+
+__device__ __forceinline__ double masked_at(const double *X, int64_t ld, int64_t r, int64_t c, int mask) {
+    if (mask == MASK_UNIT_LOWER) {
+        if (r < c) return 0.0;
+        if (r == c) return 1.0;
+    } else if (mask == MASK_UPPER) {
+        if (r > c) return 0.0;
+    }
+    return X[r + c * ld];
+}
+
+__device__ __forceinline__ void split_store(double x, int ns, __nv_bfloat16 *dst, size_t slice_stride) {
+    double r = x;
+    for (int s = 0; s < ns; ++s) {
+        const __nv_bfloat16 h = __double2bfloat16(r);
+        dst[s * slice_stride] = h;
+        r -= (double)__bfloat162float(h);
+    }
+}
+
+// BF16 slices of an FP64 operand, K-major for the MMA: operand row i holds
+// K contiguous values at dst[i * ldd + k] (ldd a multiple of 8).
+//   !transpose: operand (i, k) = stored (k, i)   (stored K x R, column-major)
+//    transpose: operand (i, k) = stored (i, k)   (stored R x K, column-major)
+// Entries k in [K, ldd) are zero.  mask applies to the stored coordinates.
+__global__ void __launch_bounds__(kThreads) split_plain_kernel(int64_t K, int64_t R, const double *src, int64_t lds,
+                                                             int mask, int ns, __nv_bfloat16 *dst, int64_t ldd,
+                                                             size_t slice_stride) {
+    const int64_t total = R * ldd;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = e % ldd, i = e / ldd;
+        const double x = (k < K) ? masked_at(src, lds, k, i, mask) : 0.0;
+        split_store(x, ns, dst + i * ldd + k, slice_stride);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) split_transpose_kernel(int64_t K, int64_t R, const double *src,
+                                                                 int64_t lds, int mask, int ns,
+                                                                 __nv_bfloat16 *dst, int64_t ldd,
+                                                                 size_t slice_stride) {
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.y * 32, k0 = (int64_t)blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int y = ty; y < 32; y += 8) {
+        const int64_t i = i0 + tx, k = k0 + y;                 // read along i (contiguous in stored column k)
+        tile[y][tx] = (i < R && k < K) ? masked_at(src, lds, i, k, mask) : 0.0;
+    }
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int64_t i = i0 + y, k = k0 + tx;                 // write along k (contiguous in dst row i)
+        if (i < R && k < ldd) split_store(tile[tx][y], ns, dst + i * ldd + k, slice_stride);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)ptr;
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D map over BF16 slices: dims (K, rows, slices), row stride ldd elements.
+bool make_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, int slices, int64_t ldd, int box_rows) {
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slices};
+    cuuint64_t strides[2] = {(cuuint64_t)ldd * 2, (cuuint64_t)ldd * (cuuint64_t)rows * 2};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t tc_smem_bytes(int BN) { return 1024 + TC_STAGES * (A_TILE_BYTES + (size_t)BN * TC_BK * 2) + 256; }
+
+int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
+
+}  // namespace
+
+size_t tc_gemm_scratch_bytes(int64_t M, int64_t N, int64_t K, int num_sms) {
+    const int64_t ldk = pad8(std::max<int64_t>(K, 1));
+    size_t b = 0;
+    b += (size_t)3 * std::max<int64_t>(M, 1) * ldk * 2 + 256;     // A slices
+    b += (size_t)3 * std::max<int64_t>(N, 1) * ldk * 2 + 256;     // B slices
+    b += (size_t)4 * num_sms * TC_BM * 128 * 4 + 256;            // split-K partials (bounded below)
+    return b;
+}
+
+gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
+    if (op.M <= 0 || op.N <= 0) return GBQR_OK;
+    if (op.nsplit < 1 || op.nsplit > 3) return GBQR_EINVAL;
+    if (op.M > (1 << 30) || op.N > (1 << 30) || op.K > (1 << 30)) return GBQR_EUNSUPPORTED;
+    const int64_t K = std::max<int64_t>(op.K, 1), ldk = pad8(K);
+    const size_t sa = (size_t)op.M * ldk, sb = (size_t)op.N * ldk;
+    const size_t need = ((size_t)3 * sa * 2 + 255) / 256 * 256 + ((size_t)3 * sb * 2 + 255) / 256 * 256;
+    if (!sc.base || need > sc.bytes) return GBQR_ENOMEM;
+    __nv_bfloat16 *As = (__nv_bfloat16 *)sc.base;
+    __nv_bfloat16 *Bs = (__nv_bfloat16 *)((char *)sc.base + ((size_t)3 * sa * 2 + 255) / 256 * 256);
+    float *partial = (float *)((char *)Bs + ((size_t)3 * sb * 2 + 255) / 256 * 256);
+    const size_t partial_cap = (sc.bytes - need) / 4;
+
+    // slices of op(A) (rows M) and of B (rows N), K-major
+    trace_begin(ex, FAM_OTHER);
+    if (op.ta) {
+        const int64_t total = op.M * ldk;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ex.num_sms * 16));
+        split_plain_kernel<<<g, kThreads, 0, ex.stream>>>(op.K, op.M, op.A, op.lda, op.maskA, op.nsplit, As, ldk, sa);
+    } else {
+        dim3 g((unsigned)((ldk + 31) / 32), (unsigned)((op.M + 31) / 32));
+        split_transpose_kernel<<<g, kThreads, 0, ex.stream>>>(op.K, op.M, op.A, op.lda, op.maskA, op.nsplit, As, ldk, sa);
+    }
+    TRY_ST(trace_end(ex, FAM_OTHER, 0.0, (8.0 + 2.0 * op.nsplit) * op.M * K));
+    trace_begin(ex, FAM_OTHER);
+    {
+        const int64_t total = op.N * ldk;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ex.num_sms * 16));
+        split_plain_kernel<<<g, kThreads, 0, ex.stream>>>(op.K, op.N, op.B, op.ldb, op.maskB, op.nsplit, Bs, ldk, sb);
+    }
+    TRY_ST(trace_end(ex, FAM_OTHER, 0.0, (8.0 + 2.0 * op.nsplit) * op.N * K));
+
+    // tile shape and split-K
+    const int BN = (((op.M + TC_BM - 1) / TC_BM) * ((op.N + 127) / 128) >= ex.num_sms) ? 128 : 64;
+    const int64_t tm = (op.M + TC_BM - 1) / TC_BM, tn = (op.N + BN - 1) / BN;
+    const int ktiles = (int)((K + TC_BK - 1) / TC_BK);
+    int S = 1;
+    if (tm * tn < ex.num_sms) S = (int)std::min<int64_t>({(ex.num_sms + tm * tn - 1) / (tm * tn), (int64_t)ktiles, 16});
+    while (S > 1 && (size_t)S * op.M * op.N > partial_cap) --S;
+    const int per = (ktiles + S - 1) / S;
+    S = (ktiles + per - 1) / per;   // every split gets at least one K tile
+
+    TcParams p;
+    p.M = (int)op.M; p.N = (int)op.N; p.K = (int)K;
+    p.ktiles_per_split = per;
+    static const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
+    p.npairs = op.nsplit == 1 ? 1 : (op.nsplit == 2 ? 3 : 6);
+    // smaller products first, the leading one last
+    for (int q = 0; q < p.npairs; ++q) {
+        p.pair_a[q] = pa[p.npairs - 1 - q];
+        p.pair_b[q] = pb[p.npairs - 1 - q];
+    }
+    p.C = op.C; p.ldc = op.ldc; p.alpha = op.alpha; p.beta = op.beta;
+    p.partial = (S > 1) ? partial : nullptr;
+    p.err = sc.err;
+
+    CUtensorMap mA, mB;
+    if (!make_map(&mA, As, K, op.M, op.nsplit, ldk, TC_BM) || !make_map(&mB, Bs, K, op.N, op.nsplit, ldk, BN))
+        return GBQR_ECUDA;
+    const size_t smem = tc_smem_bytes(BN);
+    static bool attr[64][2] = {};
+    const int bi = BN == 128 ? 1 : 0;
+    if (ex.device >= 0 && ex.device < 64 && !attr[ex.device][bi]) {
+        cudaError_t e = (BN == 128) ? cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                                    : cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return GBQR_ECUDA;
+        attr[ex.device][bi] = true;
+    }
+    dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)S);
+    trace_begin(ex, FAM_TC_GEMM);
+    if (BN == 128) tc_gemm_kernel<128><<<grid, TC_THREADS, smem, ex.stream>>>(mA, mB, p);
+    else tc_gemm_kernel<64><<<grid, TC_THREADS, smem, ex.stream>>>(mA, mB, p);
+    const double pairs_flops = 2.0 * (double)op.M * op.N * K * p.npairs;
+    TRY_ST(trace_end(ex, FAM_TC_GEMM, pairs_flops, 2.0 * p.npairs * ((double)op.M + op.N) * K));
+    if (S > 1) {
+        trace_begin(ex, FAM_OTHER);
+        const int64_t total = op.M * op.N;
+        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ex.num_sms * 16));
+        tc_reduce_kernel<<<g, kThreads, 0, ex.stream>>>((int)op.M, (int)op.N, S, partial, op.C, op.ldc, op.alpha, op.beta);
+        TRY_ST(trace_end(ex, FAM_OTHER, (double)S * total, 4.0 * S * total + 16.0 * total));
+    }
+    return GBQR_OK;
+}
+
+}  // namespace gbqr
