@@ -58,7 +58,8 @@ typedef enum {
     GBQR_ENONFINITE = 5,   /* input held NaN or Inf (reported by gbqr_sync) */
     GBQR_ERANKDEF = 6,     /* least squares: R has an exactly zero diagonal entry */
     GBQR_EBUSY = 7,        /* context busy (e.g. workspace in use by queued work) */
-    GBQR_EUNSUPPORTED = 8  /* valid request outside what this build implements */
+    GBQR_EUNSUPPORTED = 8, /* valid request outside what this build implements */
+    GBQR_ENOCONV = 9       /* least squares: mixed-precision refinement did not converge */
 } gbqr_status;
 
 /* Storage of the kernel T. */
@@ -92,7 +93,12 @@ typedef struct {
     int32_t lookahead;  /* GBQR_T_PANEL: 0 or 1 = factor panel k+1 on a
                            high-priority internal stream while the rest of
                            panel k's trailing update runs (default); -1 = off */
-    int32_t reserved[3];
+    int32_t update_prec;/* GBQR_T_PANEL trailing-update products: GBQR_FP64
+                           (default), GBQR_MIXED_BF16 (one BF16 slice) or
+                           GBQR_MIXED_SPLITBF16 (three slices, FP32-level) on
+                           the tensor cores.  Reflector generation, the TSQR
+                           R-merges and the in-panel products stay FP64. */
+    int32_t reserved[2];
 } gbqr_opts;
 
 /* Device-side record of one or more calls since the last gbqr_sync(). */
@@ -100,7 +106,9 @@ typedef struct {
     int64_t nonfinite;     /* non-zero if a NaN/Inf input was seen */
     int64_t zero_pivots;   /* reflectors whose column was exactly zero */
     int64_t rankdef_col;   /* least squares: first j with R(j,j) == 0, else -1 */
-    int64_t reserved[5];
+    int64_t refine_iters;  /* least squares, mixed precision: refinement steps taken */
+    double refine_last;    /* ... and ||dx|| / ||x|| of the last step */
+    int64_t reserved[3];
 } gbqr_info;
 
 /* Per-kernel-family totals of traced launches (see gbqr_trace_enable). */
@@ -189,13 +197,22 @@ GBQR_API gbqr_status gbqr_form_q(gbqr_ctx *ctx, int64_t m, int64_t n, const doub
 
 /* ---- least squares (Section 2.1 problem, solved through the QR) -------- */
 
-/* x = argmin ||A x - b||_2 for m x n A of full column rank (m >= n):
- * factor a workspace copy of A (A itself is not modified), c = Q^T b,
- * x = R^{-1} c(0:n) by blocked back substitution.  b has m entries, x
- * receives n.  prec must be GBQR_FP64 in this build (others: EUNSUPPORTED).
- * info (may be NULL) receives rankdef_col after an internal synchronisation;
- * an exactly zero R(j,j) gives ERANKDEF.  Synchronous: returns after x is
- * written.  Errors: EINVAL, ENOMEM, ECUDA, ERANKDEF, EUNSUPPORTED. */
+/* x = argmin ||A x - b||_2 for m x n A of full column rank (m >= n)
+ * (Section 2.1), through the QR of a workspace copy of A (A itself is not
+ * modified): c = Q^T b, x = R^{-1} c(0:n) by blocked back substitution.
+ *   prec GBQR_FP64: every step in FP64 (the backward-stable solution).
+ *   prec GBQR_MIXED_SPLITBF16 / GBQR_MIXED_BF16: the trailing-update
+ *     products of the factorization run on the tensor cores (3 or 1 BF16
+ *     slices, FP32 accumulation; reflectors and R-merges stay FP64), then
+ *     the solution is refined on the augmented system [I A; A^T 0][r; x] =
+ *     [b; 0] with FP64 residuals until ||dx|| / ||x|| stops decreasing or
+ *     falls below 1e-16 (at most 40 steps).  Converges when kappa(A) times
+ *     the factorization's precision is well below 1.
+ * b has m entries, x receives n (device pointers).  info (may be NULL)
+ * receives rankdef_col and, for the mixed path, refine_iters / refine_last.
+ * Synchronous: returns after x is written.
+ * Errors: EINVAL, ENOMEM, ECUDA, ERANKDEF (an exactly zero R(j,j)),
+ * ENOCONV (mixed refinement stalled above 1e-12), EUNSUPPORTED. */
 GBQR_API gbqr_status gbqr_ls_solve(gbqr_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
                           const double *b, double *x, int prec, gbqr_info *info);
 

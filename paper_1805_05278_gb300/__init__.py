@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libgbqr.so")
 
 # status codes (gbqr_status)
 GBQR_OK, GBQR_EINVAL, GBQR_ENOMEM, GBQR_ECUDA, GBQR_ETIMEOUT = 0, 1, 2, 3, 4
-GBQR_ENONFINITE, GBQR_ERANKDEF, GBQR_EBUSY, GBQR_EUNSUPPORTED = 5, 6, 7, 8
+GBQR_ENONFINITE, GBQR_ERANKDEF, GBQR_EBUSY, GBQR_EUNSUPPORTED, GBQR_ENOCONV = 5, 6, 7, 8, 9
 # T layouts (gbqr_t_layout) and precisions (gbqr_prec)
 GBQR_T_FULL, GBQR_T_PANEL = 0, 1
 GBQR_FP64, GBQR_MIXED_BF16, GBQR_MIXED_SPLITBF16, GBQR_FP32 = 0, 1, 2, 3
@@ -35,12 +35,13 @@ _P = ctypes.c_void_p
 class gbqr_opts(ctypes.Structure):
     _fields_ = [("cutoff_b", ctypes.c_int32), ("panel_nb", ctypes.c_int32),
                 ("leaf_rows", ctypes.c_int32), ("fanout", ctypes.c_int32),
-                ("lookahead", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("lookahead", ctypes.c_int32), ("update_prec", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class gbqr_info(ctypes.Structure):
     _fields_ = [("nonfinite", ctypes.c_int64), ("zero_pivots", ctypes.c_int64),
-                ("rankdef_col", ctypes.c_int64), ("reserved", ctypes.c_int64 * 5)]
+                ("rankdef_col", ctypes.c_int64), ("refine_iters", ctypes.c_int64),
+                ("refine_last", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
 
 
 class gbqr_trace_rec(ctypes.Structure):
@@ -117,10 +118,11 @@ def check(status: int, what: str) -> int:
 
 
 def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int = 0,
-         lookahead: int = 0) -> gbqr_opts:
+         lookahead: int = 0, update_prec: int = GBQR_FP64) -> gbqr_opts:
     o = gbqr_opts()
     o.cutoff_b, o.panel_nb, o.leaf_rows, o.fanout = cutoff_b, panel_nb, leaf_rows, fanout
     o.lookahead = lookahead
+    o.update_prec = update_prec
     return o
 
 

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -71,6 +72,7 @@ struct Params {
     int leaf_rows = 0;
     int fanout = kDefaultFanout;
     bool lookahead = true;
+    int nsplit = 0;        // 0: FP64 updates; 1..3: split-BF16 tensor-core updates
 };
 
 bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
@@ -86,6 +88,9 @@ bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
         if (o->fanout) r.fanout = o->fanout;
         if (o->lookahead < -1 || o->lookahead > 1) return false;
         if (o->lookahead == -1) r.lookahead = false;
+        if (o->update_prec == GBQR_MIXED_BF16) r.nsplit = 1;
+        else if (o->update_prec == GBQR_MIXED_SPLITBF16) r.nsplit = 3;
+        else if (o->update_prec != GBQR_FP64) return false;
     }
     r.nb = std::max<int64_t>(1, r.nb);
     *p = r;
@@ -97,6 +102,7 @@ struct Layout {
     size_t partial = 0, gcount = 0, tR = 0, tT = 0, tY = 0, tX = 0, tcount = 0;
     size_t M1 = 0, M2 = 0, bigA = 0, bigT = 0, vec = 0;
     size_t partial2 = 0, gcount2 = 0, M1b = 0, M2b = 0;   // second lane (look-ahead panel stream)
+    size_t tc = 0, n_tc = 0;                              // tensor-core slices (mixed updates)
     size_t total = 0;
     size_t n_partial = 0, n_gcount = 0, n_M = 0, n_Mb = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
     TsqrPlan tsqr;
@@ -134,9 +140,16 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     L.gcount2 = take(align_up(L.n_gcount * 4, 16));
     L.M1b = take(L.n_Mb * 8);
     L.M2b = take(L.n_Mb * 8);
+    if (pr.nsplit > 0) {
+        // W1 = V^T C (M = nb, N <= n, K <= m) and C -= V W2 (M <= m, N <= n, K = nb)
+        L.n_tc = std::max(tc_gemm_scratch_bytes(nb, std::max<int64_t>(n, 1), std::max<int64_t>(m, 1), num_sms),
+                          tc_gemm_scratch_bytes(std::max<int64_t>(m, 1), std::max<int64_t>(n, 1), nb, num_sms));
+        L.tc = take(L.n_tc);
+    }
     L.bigA = take(L.n_bigA * 8);
     L.bigT = take(L.n_bigT * 8);
-    L.vec = take((size_t)std::max<int64_t>(m, 1) * 8);
+    // least squares: vectors f, r (m) and x, dx, g (n) of the refinement
+    L.vec = take(((size_t)3 * std::max<int64_t>(m, 1) + 4 * (size_t)std::max<int64_t>(n, 1) + 16) * 8);
     L.total = off;
     return L;
 }
@@ -180,6 +193,7 @@ struct Work {
     TsqrWork tw;
     double *M1, *M2, *bigA, *bigT, *vec;
     size_t n_M;                      // capacity of M1 / M2 of this lane
+    TcScratch tcs;                   // tensor-core scratch (main lane, mixed updates)
     GemmScratch gs2;
     double *M1b, *M2b;
 
@@ -192,6 +206,7 @@ struct Work {
         o.M1 = M1b;
         o.M2 = M2b;
         o.n_M = L.n_Mb;
+        o.tcs = TcScratch();
         return o;
     }
 };
@@ -243,6 +258,9 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
     w->gs2.ncounters = w->L.n_gcount;
     w->M1b = (double *)(base + w->L.M1b);
     w->M2b = (double *)(base + w->L.M2b);
+    w->tcs.base = w->L.n_tc ? (void *)(base + w->L.tc) : nullptr;
+    w->tcs.bytes = w->L.n_tc;
+    w->tcs.err = &cx->dinfo->timeout;
     // arrival counters start at zero (every kernel leaves them zero again)
     if (cudaMemsetAsync(base + w->L.gcount, 0, w->L.counter_bytes, cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
@@ -256,9 +274,39 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
 // C (mr x nc) <- (I - V op(T) V^T) C; op(T) = T^T when trans.  V is the unit
 // lower trapezoidal mr x kv basis, T the kv x kv upper triangular kernel.
 gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
-                        const double *V, int64_t ldv, const double *T, int64_t ldt, double *C, int64_t ldc) {
+                        const double *V, int64_t ldv, const double *T, int64_t ldt, double *C, int64_t ldc,
+                        int nsplit = 0) {
     if (mr <= 0 || nc <= 0 || kv <= 0) return GBQR_OK;
     if ((size_t)kv * (size_t)nc > w.n_M) return GBQR_ENOMEM;
+    if (nc == 1) {
+        // one vector: matrix-vector products instead of 1-column GEMM tiles
+        TRY(gemv_t(w.ex, mr, kv, V, ldv, C, 1.0, 0.0, w.M1, MASK_UNIT_LOWER));
+        GemmOp h;
+        h.M = kv; h.N = 1; h.K = kv;
+        h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
+        h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
+        TRY(gemm(w.ex, h, w.gs));
+        return gemv_n(w.ex, mr, kv, V, ldv, w.M2, -1.0, 1.0, C, w.gs.partial, w.gs.partial_elems, MASK_UNIT_LOWER);
+    }
+    if (nsplit > 0 && w.tcs.base) {
+        // mixed precision: the two large products on the tensor cores
+        // (split-BF16, FP32 accumulation), the small T product in FP64
+        TcGemmOp g;
+        g.M = kv; g.N = nc; g.K = mr;
+        g.A = V; g.lda = ldv; g.ta = true; g.maskA = MASK_UNIT_LOWER;
+        g.B = C; g.ldb = ldc; g.C = w.M1; g.ldc = kv; g.nsplit = nsplit;
+        TRY(tc_gemm(w.ex, g, w.tcs));
+        GemmOp h;
+        h.M = kv; h.N = nc; h.K = kv;
+        h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
+        h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
+        TRY(gemm(w.ex, h, w.gs));
+        TcGemmOp u;
+        u.M = mr; u.N = nc; u.K = kv;
+        u.A = V; u.lda = ldv; u.ta = false; u.maskA = MASK_UNIT_LOWER;
+        u.B = w.M2; u.ldb = kv; u.C = C; u.ldc = ldc; u.alpha = -1.0; u.beta = 1.0; u.nsplit = nsplit;
+        return tc_gemm(w.ex, u, w.tcs);
+    }
     GemmOp g;
     g.M = kv; g.N = nc; g.K = mr;
     g.A = V; g.lda = ldv; g.ta = true; g.maskA = MASK_UNIT_LOWER;
@@ -355,7 +403,8 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda,
             double *Tk = T + j0 * ldt;
             TRY(qr_eg(w, m - j0, wd, Ap, lda, Tk, ldt));
             if (j0 + wd < n)
-                TRY(apply_block(w, true, m - j0, n - j0 - wd, wd, Ap, lda, Tk, ldt, A + j0 + (j0 + wd) * lda, lda));
+                TRY(apply_block(w, true, m - j0, n - j0 - wd, wd, Ap, lda, Tk, ldt, A + j0 + (j0 + wd) * lda, lda,
+                                w.pr.nsplit));
         }
         return GBQR_OK;
     }
@@ -376,14 +425,15 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda,
         const double *Vk = A + j0 + j0 * lda;
         const double *Tk = T + j0 * ldt;
         // panel k+1's columns first ...
-        TRY(apply_block(w, true, m - j0, w1, wd, Vk, lda, Tk, ldt, A + j0 + j1 * lda, lda));
+        TRY(apply_block(w, true, m - j0, w1, wd, Vk, lda, Tk, ldt, A + j0 + j1 * lda, lda, w.pr.nsplit));
         if (cudaEventRecord(cx->ev_ready, ms) != cudaSuccess || cudaStreamWaitEvent(ss, cx->ev_ready, 0) != cudaSuccess)
             return GBQR_ECUDA;
         // ... then panel k+1 on the side stream, concurrently with the rest of the update
         TRY(qr_eg(wp, m - j1, w1, A + j1 + j1 * lda, lda, T + j1 * ldt, ldt));
         if (cudaEventRecord(cx->ev_panel, ss) != cudaSuccess) return GBQR_ECUDA;
         if (j1 + w1 < n)
-            TRY(apply_block(w, true, m - j0, n - j1 - w1, wd, Vk, lda, Tk, ldt, A + j0 + (j1 + w1) * lda, lda));
+            TRY(apply_block(w, true, m - j0, n - j1 - w1, wd, Vk, lda, Tk, ldt, A + j0 + (j1 + w1) * lda, lda,
+                            w.pr.nsplit));
     }
     return GBQR_OK;
 }
@@ -450,6 +500,7 @@ const char *gbqr_strerror(gbqr_status s) {
         case GBQR_ERANKDEF: return "rank deficient (zero diagonal in R)";
         case GBQR_EBUSY: return "context busy";
         case GBQR_EUNSUPPORTED: return "unsupported in this build";
+        case GBQR_ENOCONV: return "iterative refinement did not converge";
     }
     return "unknown status";
 }
@@ -636,12 +687,17 @@ gbqr_status gbqr_form_q(gbqr_ctx *cx, int64_t m, int64_t n, const double *VR, in
 gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, int64_t lda,
                           const double *b, double *x, int prec, gbqr_info *info) {
     if (!cx) return GBQR_EINVAL;
-    if (prec != GBQR_FP64) return GBQR_EUNSUPPORTED;
+    if (prec != GBQR_FP64 && prec != GBQR_MIXED_BF16 && prec != GBQR_MIXED_SPLITBF16) return GBQR_EUNSUPPORTED;
     if (m < n || n < 0 || lda < std::max<int64_t>(1, m)) return GBQR_EINVAL;
+    if (info) memset(info, 0, sizeof *info);
+    if (info) info->rankdef_col = -1;
     if (n == 0) return GBQR_OK;
     if (!A || !b || !x) return GBQR_EINVAL;
     Params pr;
-    resolve(nullptr, m, n, &pr);
+    gbqr_opts o;
+    memset(&o, 0, sizeof o);
+    o.update_prec = prec;
+    if (!resolve(&o, m, n, &pr)) return GBQR_EINVAL;
     Work w;
     TRY(begin_work(cx, m, n, GBQR_T_PANEL, pr, &w));
     const int64_t nb = std::min<int64_t>(pr.nb, n);
@@ -649,22 +705,64 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     static const long long kNone = LLONG_MAX;
     if (cudaMemcpyAsync(&di->rankdef, &kNone, sizeof kNone, cudaMemcpyHostToDevice, cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
+    double *f = w.vec, *r = f + m, *nrm = r + m;          // nrm: 2 doubles (+ padding)
+    double *dx = nrm + 16, *g = dx + n;
+    // factor a copy of A; c = Q^T b; x = R^{-1} c(0:n)
     TRY(copy_matrix(w.ex, m, n, A, lda, w.bigA, m));
     TRY(factor_device(w, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL));
-    TRY(copy_matrix(w.ex, m, 1, b, m, w.vec, m));
-    TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, w.vec, m, false));
-    TRY(copy_matrix(w.ex, n, 1, w.vec, n, x, n));
+    TRY(copy_matrix(w.ex, m, 1, b, m, f, m));
+    TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
+    TRY(copy_matrix(w.ex, n, 1, f, n, x, n));
     TRY(trsv_upper(w.ex, n, w.bigA, m, x, &di->rankdef));
+    int iters = 0;
+    double last = 0.0;
+    bool converged = (prec == GBQR_FP64);
+    if (!converged) {
+        // Refinement on the augmented system [I A; A^T 0][r; x] = [b; 0] with
+        // FP64 residuals; each correction solved with the mixed QR:
+        //   f = b - r - A x,  g = -A^T r,  h = R^{-T} g,  d = Q^T f,
+        //   dx = R^{-1}(d(0:n) - h),  dr = Q [h; d(n:m)]
+        TRY(copy_matrix(w.ex, m, 1, b, m, r, m));
+        TRY(gemv_n(w.ex, m, n, A, lda, x, -1.0, 1.0, r, w.gs.partial, w.gs.partial_elems));
+        double prev = 1e300;
+        for (iters = 1; iters <= 40; ++iters) {
+            TRY(copy_matrix(w.ex, m, 1, b, m, f, m));
+            TRY(axpby(w.ex, m, -1.0, r, 1.0, f));
+            TRY(gemv_n(w.ex, m, n, A, lda, x, -1.0, 1.0, f, w.gs.partial, w.gs.partial_elems));
+            TRY(gemv_t(w.ex, m, n, A, lda, r, -1.0, 0.0, g));
+            TRY(trsv_upper_t(w.ex, n, w.bigA, m, g, &di->rankdef));                 // g <- h
+            TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
+            TRY(copy_matrix(w.ex, n, 1, f, n, dx, n));
+            TRY(axpby(w.ex, n, -1.0, g, 1.0, dx));
+            TRY(trsv_upper(w.ex, n, w.bigA, m, dx, &di->rankdef));
+            TRY(copy_matrix(w.ex, n, 1, g, n, f, n));                               // f <- [h; d2]
+            TRY(apply_q_any(w, false, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
+            TRY(axpby(w.ex, n, 1.0, dx, 1.0, x));
+            TRY(axpby(w.ex, m, 1.0, f, 1.0, r));
+            TRY(norms2(w.ex, n, dx, x, nrm));
+            double hn[2] = {0.0, 0.0};
+            if (cudaMemcpyAsync(hn, nrm, sizeof hn, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(cx->stream) != cudaSuccess)
+                return GBQR_ECUDA;
+            last = (hn[1] > 0.0) ? std::sqrt(hn[0] / hn[1]) : 0.0;
+            if (!(last == last)) break;                                   // NaN: stop
+            if (last <= 1e-16) { converged = true; break; }
+            if (iters >= 3 && last > 0.5 * prev) { converged = last <= 1e-12; break; }
+            prev = last;
+        }
+    }
     long long rk = -1;
     if (cudaMemcpyAsync(&rk, &di->rankdef, sizeof rk, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
     if (cudaStreamSynchronize(cx->stream) != cudaSuccess) return GBQR_ECUDA;
     if (rk == LLONG_MAX) rk = -1;
     if (info) {
-        memset(info, 0, sizeof *info);
         info->rankdef_col = rk;
+        info->refine_iters = iters;
+        info->refine_last = last;
     }
-    return rk >= 0 ? GBQR_ERANKDEF : GBQR_OK;
+    if (rk >= 0) return GBQR_ERANKDEF;
+    return converged ? GBQR_OK : GBQR_ENOCONV;
 }
 
 gbqr_status gbqr_trace_enable(gbqr_ctx *cx, int on) {

@@ -136,4 +136,18 @@ gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const double *A
 gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x,
                        long long *rankdef);
 
+// x (n) <- R^{-T} x (forward substitution with the lower triangle R^T).
+gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef);
+// y = alpha A x + beta y (A m x n); partial: >= m * chunks doubles of scratch.
+// mask MASK_UNIT_LOWER treats A as a unit lower trapezoidal basis.
+gbqr_status gemv_n(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, const double *x, double alpha,
+                   double beta, double *y, double *partial, size_t partial_elems, int mask = MASK_NONE);
+// g = alpha A^T r + beta g
+gbqr_status gemv_t(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, const double *r, double alpha,
+                   double beta, double *g, int mask = MASK_NONE);
+// out[0] = ||x||^2, out[1] = ||y||^2 (n entries each)
+gbqr_status norms2(const Exec &ex, int64_t n, const double *x, const double *y, double *out);
+// y = a x + b y
+gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y);
+
 }  // namespace gbqr

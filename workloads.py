@@ -70,6 +70,18 @@ def random_reflector_product(m: int, n: int, seed: int) -> np.ndarray:
     return np.asfortranarray(q)
 
 
+def ls_problem(m: int, n: int, decades: float, seed: int, noise: float = 1e-8):
+    """Least-squares test problem: A Gaussian m x n with column j scaled by
+    10**(-decades*j/n) (condition number about 10**decades times that of the
+    Gaussian), x_true iid N(0,1), b = A x_true + noise * N(0,1).
+    Returns (A, x_true, b)."""
+    a = graded(m, n, seed, decades)
+    rng = np.random.default_rng(seed + 1)
+    x_true = rng.standard_normal(n)
+    b = a @ x_true + noise * rng.standard_normal(m)
+    return a, x_true, b
+
+
 @dataclass(frozen=True)
 class Workload:
     """One named workload: A (m x n) and an optional right-hand side b."""
