@@ -61,7 +61,46 @@ def parse():
     p.add_argument("--panel", type=int, default=0)
     p.add_argument("--leaf", type=int, default=0)
     p.add_argument("--fanout", type=int, default=0)
+    p.add_argument("--ls-solves", type=int, default=5, help="timed least-squares solves per precision (0: skip)")
+    p.add_argument("--ls-decades", type=float, default=4.0)
     return p.parse_args()
+
+
+def measure_ls(gb, ctx, dev, args):
+    """Least-squares solves (32768 x 2048, graded columns, b = A x_true + 1e-8
+    noise): FP64 path vs mixed path (tensor-core split-BF16 updates + FP64
+    refinement).  Each solve timed alone with CUDA events; solves/s = count /
+    summed time; p50 / p99 over the solves."""
+    import torch
+    m, n = 32768, 2048
+    a, xt, b = workloads.ls_problem(m, n, args.ls_decades, 11)
+    A = gb.to_colmajor(a, f"cuda:{dev}")
+    bd = torch.from_numpy(b).to(f"cuda:{dev}")
+    xtd = torch.from_numpy(xt).to(f"cuda:{dev}")
+    out, xs = {}, {}
+    stream = torch.cuda.current_stream(dev)
+    ctx = gb.Context(dev, stream)        # its own, library-grown workspace
+    for prec, name in [(gb.GBQR_FP64, "fp64"), (gb.GBQR_MIXED_SPLITBF16, "mixed_splitbf16")]:
+        x = torch.zeros(n, dtype=torch.float64, device=f"cuda:{dev}")
+        st, info = ctx.ls_solve(A, bd, x, prec)          # warm-up
+        times = []
+        for _ in range(args.ls_solves):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, info = ctx.ls_solve(A, bd, x, prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        times.sort()
+        xs[name] = x.clone()
+        out[name] = {"status": int(st), "solves_per_s": len(times) / (sum(times) * 1e-3),
+                     "p50_ms": times[len(times) // 2], "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
+                     "refine_iters": int(info.refine_iters),
+                     "rel_err_vs_xtrue": float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))}
+    out["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(xs["mixed_splitbf16"] - xs["fp64"]) / torch.linalg.norm(xs["fp64"]))
+    out["workload"] = f"ls graded {m}x{n}, decades {args.ls_decades}, b = A x_true + 1e-8 N(0,1), seed 11"
+    ctx.close()
+    return out
 
 
 # ------------------------------------------------------------- multi-rank
@@ -283,8 +322,8 @@ def run_gbqr(args):
             e2e_times.append(dt)
     e2e_value = w.flops * world / statistics.median(e2e_times) / 1e12 if e2e_times else None
 
-    # check the step's output against properties (cheap sampled parity lives in the tests)
     st, info = ctx.sync()
+    ls = measure_ls(gb, None, dev, args) if (args.ls_solves > 0 and rank == 0) else None
 
     gemm = trace.get("gemm", {})
     achieved = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm.get("ms") else None
@@ -323,6 +362,7 @@ def run_gbqr(args):
             "families": fams,
             "clocks": clocks,
             "cpu_baseline": cpu,
+            "ls": ls,
             "status_after": int(st),
         }
         print(json.dumps(line), flush=True)

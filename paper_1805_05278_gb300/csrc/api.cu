@@ -62,7 +62,7 @@ struct EventTracer final : Tracer {
     }
 };
 
-const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "other"};
+const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "trsv", "gemv", "other"};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -281,11 +281,15 @@ gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
     if (nc == 1) {
         // one vector: matrix-vector products instead of 1-column GEMM tiles
         TRY(gemv_t(w.ex, mr, kv, V, ldv, C, 1.0, 0.0, w.M1, MASK_UNIT_LOWER));
-        GemmOp h;
-        h.M = kv; h.N = 1; h.K = kv;
-        h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
-        h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
-        TRY(gemm(w.ex, h, w.gs));
+        if (kv <= kThreads) {
+            TRY(trmv_upper(w.ex, (int)kv, T, ldt, trans, w.M1, w.M2));
+        } else {
+            GemmOp h;
+            h.M = kv; h.N = 1; h.K = kv;
+            h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
+            h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
+            TRY(gemm(w.ex, h, w.gs));
+        }
         return gemv_n(w.ex, mr, kv, V, ldv, w.M2, -1.0, 1.0, C, w.gs.partial, w.gs.partial_elems, MASK_UNIT_LOWER);
     }
     if (nsplit > 0 && w.tcs.base) {

@@ -49,75 +49,9 @@ __global__ void __launch_bounds__(kThreads) nonfinite_kernel(int64_t m, int64_t 
 
 constexpr int kTrsvBlock = 64;
 
-// Solve the diagonal block R(j0:j0+s, j0:j0+s) x = x(j0:j0+s) in place
-// (column-oriented back substitution, one CTA of kTrsvBlock threads).
-__global__ void __launch_bounds__(kTrsvBlock) trsv_diag_kernel(int64_t j0, int s, const double *R, int64_t ldr,
-                                                              double *x, long long *rankdef) {
-    __shared__ double xs[kTrsvBlock];
-    const int t = threadIdx.x;
-    if (t < s) xs[t] = x[j0 + t];
-    __syncthreads();
-    for (int j = s - 1; j >= 0; --j) {
-        const double d = R[(j0 + j) + (j0 + j) * ldr];
-        if (t == 0) {
-            if (d == 0.0) atomicMin(rankdef, (long long)(j0 + j));
-            xs[j] = xs[j] / d;
-        }
-        __syncthreads();
-        if (t < j) xs[t] = fma(-R[(j0 + t) + (j0 + j) * ldr], xs[j], xs[t]);
-        __syncthreads();
-    }
-    if (t < s) x[j0 + t] = xs[t];
-}
 
-// x(0:j0) -= R(0:j0, j0:j0+s) x(j0:j0+s), one thread per row.
-__global__ void __launch_bounds__(kThreads) trsv_update_kernel(int64_t j0, int s, const double *R, int64_t ldr,
-                                                             double *x) {
-    __shared__ double xb[kTrsvBlock];
-    if (threadIdx.x < s) xb[threadIdx.x] = x[j0 + threadIdx.x];
-    __syncthreads();
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= j0) return;
-    double acc = 0.0;
-    for (int l = 0; l < s; ++l) acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
-    x[i] -= acc;
-}
 
-// x(j0+s:n) -= R(j0:j0+s, j0+s:n)^T x(j0:j0+s): one warp per later column.
-__global__ void __launch_bounds__(kThreads) trsv_t_update_kernel(int64_t n, int64_t j0, int s, const double *R,
-                                                               int64_t ldr, double *x) {
-    __shared__ double xb[kTrsvBlock];
-    if (threadIdx.x < s) xb[threadIdx.x] = x[j0 + threadIdx.x];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t i = j0 + s + (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    double acc = 0.0;
-    for (int l = lane; l < s; l += 32) acc = fma(R[(j0 + l) + i * ldr], xb[l], acc);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) x[i] -= acc;
-}
 
-// Solve R(j0:j0+s, j0:j0+s)^T y = x(j0:j0+s) in place (forward substitution).
-__global__ void __launch_bounds__(kTrsvBlock) trsv_t_diag_kernel(int64_t j0, int s, const double *R, int64_t ldr,
-                                                                double *x, long long *rankdef) {
-    __shared__ double xs[kTrsvBlock];
-    const int t = threadIdx.x;
-    if (t < s) xs[t] = x[j0 + t];
-    __syncthreads();
-    for (int j = 0; j < s; ++j) {
-        const double d = R[(j0 + j) + (j0 + j) * ldr];
-        if (t == 0) {
-            if (d == 0.0) atomicMin(rankdef, (long long)(j0 + j));
-            xs[j] = xs[j] / d;
-        }
-        __syncthreads();
-        if (t > j && t < s) xs[t] = fma(-R[(j0 + j) + (j0 + t) * ldr], xs[j], xs[t]);
-        __syncthreads();
-    }
-    if (t < s) x[j0 + t] = xs[t];
-}
 
 // y(m) = alpha * A(m x n) x + beta * y, split over column chunks with FP64
 // partials P[chunk][m], then summed in a fixed order (deterministic).
@@ -195,6 +129,129 @@ __global__ void __launch_bounds__(kThreads) axpby_kernel(int64_t n, double a, co
         y[i] = (b == 0.0) ? a * x[i] : fma(a, x[i], b * y[i]);
 }
 
+// One warp solves the s x s diagonal block of R whose rows/columns start at
+// jb, with the right-hand side in xs[0:s] (shared memory): back substitution
+// (transpose = false, R upper) or forward substitution with R^T.  The block
+// is staged in shared memory by the whole CTA first; pivots are used through
+// their reciprocals so that each step is one multiply, one shuffle and one
+// FMA on the critical path.
+__device__ void warp_block_solve(int64_t jb, int s, const double *R, int64_t ldr, double *xs, double *Rs,
+                                 bool transpose, long long *rankdef) {
+    for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+        const int i = idx % s, c = idx / s;
+        Rs[i + c * kTrsvBlock] = R[(jb + i) + (jb + c) * ldr];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double c0 = (lane < s) ? xs[lane] : 0.0, c1 = (lane + 32 < s) ? xs[lane + 32] : 0.0;
+        double r0 = 0.0, r1 = 0.0;
+        if (lane < s) {
+            const double d = Rs[lane + lane * kTrsvBlock];
+            if (d == 0.0) atomicMin(rankdef, (long long)(jb + lane));
+            r0 = 1.0 / d;
+        }
+        if (lane + 32 < s) {
+            const double d = Rs[(lane + 32) + (lane + 32) * kTrsvBlock];
+            if (d == 0.0) atomicMin(rankdef, (long long)(jb + lane + 32));
+            r1 = 1.0 / d;
+        }
+        for (int t = 0; t < s; ++t) {
+            const int j = transpose ? t : s - 1 - t;
+            const bool hi = j >= 32;
+            const double mine = hi ? c1 * r1 : c0 * r0;
+            const double xj = __shfl_sync(0xffffffffu, mine, j & 31);
+            if ((j & 31) == lane) { if (hi) c1 = xj; else c0 = xj; }
+            // remaining rows: i < j (back substitution) or i > j (forward, R^T)
+            const int i0 = lane, i1 = lane + 32;
+            if (!transpose) {
+                if (i0 < j) c0 = fma(-Rs[i0 + j * kTrsvBlock], xj, c0);
+                if (i1 < j) c1 = fma(-Rs[i1 + j * kTrsvBlock], xj, c1);
+            } else {
+                if (i0 > j && i0 < s) c0 = fma(-Rs[j + i0 * kTrsvBlock], xj, c0);
+                if (i1 > j && i1 < s) c1 = fma(-Rs[j + i1 * kTrsvBlock], xj, c1);
+            }
+        }
+        if (lane < s) xs[lane] = c0;
+        if (lane + 32 < s) xs[lane + 32] = c1;
+    }
+    __syncthreads();
+}
+
+// Back substitution R x = c, one launch per block (from the bottom): apply
+// the just-solved block x(j0:j0+s) to rows [0, j0) - each CTA owns 256 rows -
+// then the CTA owning the block just above, rows [jn, j0), solves it.
+__global__ void __launch_bounds__(kThreads) trsv_step_kernel(int64_t j0, int s, int64_t jn, int sn, const double *R,
+                                                           int64_t ldr, double *x, long long *rankdef) {
+    __shared__ double xb[kTrsvBlock];
+    __shared__ double xs[kTrsvBlock];
+    __shared__ double Rs[kTrsvBlock * kTrsvBlock];
+    if (threadIdx.x < s) xb[threadIdx.x] = x[j0 + threadIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+    if (i < j0 && s > 0) {
+        double acc = 0.0;
+        for (int l = 0; l < s; ++l) acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
+        x[i] -= acc;
+    }
+    const int64_t r0 = (int64_t)blockIdx.x * kThreads;
+    if (sn > 0 && jn >= r0 && jn < r0 + kThreads) {
+        __syncthreads();                 // this CTA's rows [jn, j0) are final
+        __threadfence_block();
+        if (threadIdx.x < sn) xs[threadIdx.x] = x[jn + threadIdx.x];
+        __syncthreads();
+        warp_block_solve(jn, sn, R, ldr, xs, Rs, false, rankdef);
+        if (threadIdx.x < sn) x[jn + threadIdx.x] = xs[threadIdx.x];
+    }
+}
+
+// Forward substitution R^T h = g, one launch per block (from the top): apply
+// the just-solved block h(jp:jp+sp) to entries [jp+sp, n) - each CTA owns 64
+// entries, one warp per entry - then the CTA owning the next block solves it.
+__global__ void __launch_bounds__(kThreads) trsv_t_step_kernel(int64_t n, int64_t jp, int sp, int sn,
+                                                             const double *R, int64_t ldr, double *x,
+                                                             long long *rankdef) {
+    __shared__ double xb[kTrsvBlock];
+    __shared__ double xs[kTrsvBlock];
+    __shared__ double Rs[kTrsvBlock * kTrsvBlock];
+    if (threadIdx.x < sp) xb[threadIdx.x] = x[jp + threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t e0 = jp + sp + (int64_t)blockIdx.x * kTrsvBlock;   // first entry of this CTA
+    if (sp > 0) {
+        for (int q = wid; q < kTrsvBlock; q += kThreads / 32) {
+            const int64_t i = e0 + q;
+            if (i >= n) break;
+            double acc = 0.0;
+            for (int l = lane; l < sp; l += 32) acc = fma(R[(jp + l) + i * ldr], xb[l], acc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) x[i] -= acc;
+        }
+    }
+    if (blockIdx.x == 0 && sn > 0) {
+        __syncthreads();
+        __threadfence_block();
+        if (threadIdx.x < sn) xs[threadIdx.x] = x[e0 + threadIdx.x];
+        __syncthreads();
+        warp_block_solve(e0, sn, R, ldr, xs, Rs, true, rankdef);
+        if (threadIdx.x < sn) x[e0 + threadIdx.x] = xs[threadIdx.x];
+    }
+}
+
+// y = op(T) w for a k x k upper triangular T (k <= kThreads), one CTA.
+__global__ void __launch_bounds__(kThreads) trmv_kernel(int k, const double *T, int64_t ldt, bool trans,
+                                                      const double *w, double *y) {
+    const int i = threadIdx.x;
+    if (i >= k) return;
+    double acc = 0.0;
+    if (!trans)
+        for (int l = i; l < k; ++l) acc = fma(T[i + (int64_t)l * ldt], w[l], acc);
+    else
+        for (int l = 0; l <= i; ++l) acc = fma(T[l + (int64_t)i * ldt], w[l], acc);
+    y[i] = acc;
+}
+
 unsigned grid_for(int64_t elems, int num_sms) {
     const int64_t want = (elems + kThreads - 1) / kThreads;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * 8));
@@ -233,39 +290,48 @@ gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const double *A
 }
 
 gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef) {
-    for (int64_t j0 = ((n - 1) / kTrsvBlock) * kTrsvBlock; j0 >= 0 && n > 0; j0 -= kTrsvBlock) {
-        const int s = (int)std::min<int64_t>(kTrsvBlock, n - j0);
-        trace_begin(ex, FAM_OTHER);
-        trsv_diag_kernel<<<1, kTrsvBlock, 0, ex.stream>>>(j0, s, R, ldr, x, rankdef);
-        gbqr_status st = trace_end(ex, FAM_OTHER, (double)s * s, 8.0 * s * s / 2);
-        if (st != GBQR_OK) return st;
-        if (j0 > 0) {
-            trace_begin(ex, FAM_OTHER);
-            trsv_update_kernel<<<(unsigned)((j0 + kThreads - 1) / kThreads), kThreads, 0, ex.stream>>>(j0, s, R, ldr, x);
-            st = trace_end(ex, FAM_OTHER, 2.0 * j0 * s, 8.0 * j0 * s);
-            if (st != GBQR_OK) return st;
-        }
+    if (n <= 0) return GBQR_OK;
+    const int64_t nblk = (n + kTrsvBlock - 1) / kTrsvBlock;
+    // launch k applies block k (solved) and solves block k-1; the first
+    // launch applies nothing and solves the last block
+    for (int64_t k = nblk; k >= 1; --k) {
+        const int64_t j0 = (k == nblk) ? n : k * kTrsvBlock;
+        const int s = (k == nblk) ? 0 : (int)std::min<int64_t>(kTrsvBlock, n - j0);
+        const int64_t jn = (k - 1) * kTrsvBlock;
+        const int sn = (int)std::min<int64_t>(kTrsvBlock, n - jn);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, (j0 + kThreads - 1) / kThreads);
+        trace_begin(ex, FAM_TRSV);
+        trsv_step_kernel<<<grid, kThreads, 0, ex.stream>>>(j0, s, jn, sn, R, ldr, x, rankdef);
+        TRY_ST(trace_end(ex, FAM_TRSV, 2.0 * j0 * s + (double)sn * sn, 8.0 * j0 * s));
     }
     return GBQR_OK;
 }
 
 gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef) {
-    for (int64_t j0 = 0; j0 < n; j0 += kTrsvBlock) {
-        const int s = (int)std::min<int64_t>(kTrsvBlock, n - j0);
-        trace_begin(ex, FAM_OTHER);
-        trsv_t_diag_kernel<<<1, kTrsvBlock, 0, ex.stream>>>(j0, s, R, ldr, x, rankdef);
-        gbqr_status st = trace_end(ex, FAM_OTHER, (double)s * s, 8.0 * s * s / 2);
-        if (st != GBQR_OK) return st;
-        const int64_t rest = n - j0 - s;
-        if (rest > 0) {
-            trace_begin(ex, FAM_OTHER);
-            const int per = kThreads / 32;
-            trsv_t_update_kernel<<<(unsigned)((rest + per - 1) / per), kThreads, 0, ex.stream>>>(n, j0, s, R, ldr, x);
-            st = trace_end(ex, FAM_OTHER, 2.0 * rest * s, 8.0 * rest * s);
-            if (st != GBQR_OK) return st;
-        }
+    if (n <= 0) return GBQR_OK;
+    const int64_t nblk = (n + kTrsvBlock - 1) / kTrsvBlock;
+    // launch k applies block k-1 (solved) and solves block k; the first
+    // launch applies nothing and solves block 0
+    for (int64_t k = 0; k < nblk; ++k) {
+        const int64_t jp = (k == 0) ? 0 : (k - 1) * kTrsvBlock;
+        const int sp = (k == 0) ? 0 : kTrsvBlock;
+        const int64_t jk = k * kTrsvBlock;
+        const int sn = (int)std::min<int64_t>(kTrsvBlock, n - jk);
+        const int64_t rest = n - (jp + sp);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, (rest + kTrsvBlock - 1) / kTrsvBlock);
+        trace_begin(ex, FAM_TRSV);
+        trsv_t_step_kernel<<<grid, kThreads, 0, ex.stream>>>(n, jp, sp, sn, R, ldr, x, rankdef);
+        TRY_ST(trace_end(ex, FAM_TRSV, 2.0 * rest * sp + (double)sn * sn, 8.0 * rest * sp));
     }
     return GBQR_OK;
+}
+
+gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool trans, const double *w, double *y) {
+    if (k <= 0) return GBQR_OK;
+    if (k > kThreads) return GBQR_EUNSUPPORTED;
+    trace_begin(ex, FAM_GEMV);
+    trmv_kernel<<<1, kThreads, 0, ex.stream>>>(k, T, ldt, trans, w, y);
+    return trace_end(ex, FAM_GEMV, (double)k * k, 4.0 * k * k);
 }
 
 gbqr_status gemv_n(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, const double *x, double alpha,
@@ -277,21 +343,21 @@ gbqr_status gemv_n(const Exec &ex, int64_t m, int64_t n, const double *A, int64_
     if ((size_t)m > partial_elems) return GBQR_ENOMEM;
     const int64_t chunk = (std::max<int64_t>(n, 1) + nchunks - 1) / nchunks;
     nchunks = (std::max<int64_t>(n, 1) + chunk - 1) / chunk;
-    trace_begin(ex, FAM_OTHER);
+    trace_begin(ex, FAM_GEMV);
     gemv_n_partial_kernel<<<dim3((unsigned)rowblocks, (unsigned)nchunks), kThreads, 0, ex.stream>>>(m, n, chunk, A, lda, x, partial, mask);
-    TRY_ST(trace_end(ex, FAM_OTHER, 2.0 * m * n, 8.0 * m * n));
-    trace_begin(ex, FAM_OTHER);
+    TRY_ST(trace_end(ex, FAM_GEMV, 2.0 * m * n, 8.0 * m * n));
+    trace_begin(ex, FAM_GEMV);
     gemv_n_reduce_kernel<<<(unsigned)rowblocks, kThreads, 0, ex.stream>>>(m, (int)nchunks, partial, alpha, beta, y);
-    return trace_end(ex, FAM_OTHER, (double)nchunks * m, 8.0 * (nchunks + 2) * m);
+    return trace_end(ex, FAM_GEMV, (double)nchunks * m, 8.0 * (nchunks + 2) * m);
 }
 
 gbqr_status gemv_t(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, const double *r, double alpha,
                    double beta, double *g, int mask) {
     if (n <= 0) return GBQR_OK;
     const int per = kThreads / 32;
-    trace_begin(ex, FAM_OTHER);
+    trace_begin(ex, FAM_GEMV);
     gemv_t_kernel<<<(unsigned)((n + per - 1) / per), kThreads, 0, ex.stream>>>(m, n, A, lda, r, alpha, beta, g, mask);
-    return trace_end(ex, FAM_OTHER, 2.0 * m * n, 8.0 * m * n);
+    return trace_end(ex, FAM_GEMV, 2.0 * m * n, 8.0 * m * n);
 }
 
 gbqr_status norms2(const Exec &ex, int64_t n, const double *x, const double *y, double *out) {

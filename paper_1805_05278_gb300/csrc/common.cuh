@@ -14,7 +14,7 @@ constexpr int kThreads = 256;   // threads per CTA for every kernel family
 constexpr int kMaxPanel = 64;   // largest TSQR panel width w (= cutoff b)
 
 // ---------------------------------------------------------------- tracing
-enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TSQR_RECON, FAM_OTHER, FAM_COUNT };
+enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TSQR_RECON, FAM_TRSV, FAM_GEMV, FAM_OTHER, FAM_COUNT };
 
 struct Tracer {
     virtual void begin(cudaStream_t s, Family f) = 0;
@@ -147,6 +147,8 @@ gbqr_status gemv_t(const Exec &ex, int64_t m, int64_t n, const double *A, int64_
                    double beta, double *g, int mask = MASK_NONE);
 // out[0] = ||x||^2, out[1] = ||y||^2 (n entries each)
 gbqr_status norms2(const Exec &ex, int64_t n, const double *x, const double *y, double *out);
+// y = op(T) w for k x k upper triangular T (k <= 256)
+gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool trans, const double *w, double *y);
 // y = a x + b y
 gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y);
 
