@@ -63,7 +63,46 @@ def parse():
     p.add_argument("--fanout", type=int, default=0)
     p.add_argument("--ls-solves", type=int, default=5, help="timed least-squares solves per precision (0: skip)")
     p.add_argument("--ls-decades", type=float, default=4.0)
+    p.add_argument("--batched", type=int, default=2000, help="matrices in the batched measurement (0: skip)")
+    p.add_argument("--batched-steps", type=int, default=3)
     return p.parse_args()
+
+
+def measure_batched(gb, dev, args):
+    """The batched tall-skinny workload: args.batched FP64 matrices, m
+    log-uniform in [256, 16384], n uniform in [16, 256], factored by one
+    captured graph launch of gbqr_factor_batched.  Each timed step restores
+    the inputs with one device copy, then launches the graph."""
+    import torch
+    shapes = workloads.batched_shapes(args.batched, workloads.BATCHED_SEED)
+    buf, offs = workloads.batched_device_buffer(shapes, workloads.BATCHED_SEED, f"cuda:{dev}")
+    pristine = buf.clone()
+    As = [buf[o:o + m * n].view(n, m).T for (m, n), o in zip(shapes, offs)]
+    Ts = [torch.empty((n, min(128, n)), dtype=torch.float64, device=f"cuda:{dev}").T for (m, n) in shapes]
+    stream = torch.cuda.Stream(dev)
+    ctx = gb.Context(dev, stream)
+    flops = sum(workloads.qr_flops(m, n) for (m, n) in shapes)
+    with torch.cuda.stream(stream):
+        ctx.factor_batched(As, Ts)                      # warm-up: lanes, workspace
+        torch.cuda.synchronize()
+        graph = ctx.capture(lambda: ctx.factor_batched(As, Ts))
+        launches0 = ctx.launch_count()
+        times = []
+        for _ in range(max(1, args.batched_steps)):
+            buf.copy_(pristine)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.launch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    st, _ = ctx.sync()
+    graph.close()
+    ctx.close()
+    ms = sorted(times)[len(times) // 2]
+    return {"workload": f"{len(shapes)} FP64 matrices, m log-uniform [256, 16384], n uniform [16, 256], seed {workloads.BATCHED_SEED}",
+            "total_flops": flops, "ms_per_batch": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+            "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st)}
 
 
 def measure_ls(gb, ctx, dev, args):
@@ -324,6 +363,7 @@ def run_gbqr(args):
 
     st, info = ctx.sync()
     ls = measure_ls(gb, None, dev, args) if (args.ls_solves > 0 and rank == 0) else None
+    batched = measure_batched(gb, dev, args) if (args.batched > 0 and rank == 0) else None
 
     gemm = trace.get("gemm", {})
     achieved = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm.get("ms") else None
@@ -363,6 +403,7 @@ def run_gbqr(args):
             "clocks": clocks,
             "cpu_baseline": cpu,
             "ls": ls,
+            "batched": batched,
             "status_after": int(st),
         }
         print(json.dumps(line), flush=True)

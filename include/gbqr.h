@@ -175,6 +175,40 @@ GBQR_API gbqr_status gbqr_factor(gbqr_ctx *ctx, int64_t m, int64_t n, double *A,
 /* Default top-level panel width for GBQR_T_PANEL on an m x n problem. */
 GBQR_API int64_t gbqr_default_panel_nb(int64_t m, int64_t n);
 
+/* ---- batched factorization and graph capture ---------------------------- */
+
+/* count independent QR factorizations (the 1D-CAQR-EG instance of Section 6
+ * for each matrix): A[i] (m[i] x n[i], lda[i], device) is factored in place
+ * exactly as gbqr_factor does with GBQR_T_PANEL, T[i] (ldt[i] x n[i]) receives
+ * its panel kernels.  m, n, A, lda, T, ldt are HOST arrays of count entries.
+ * The matrices are spread over up to 16 internal streams (largest first, to
+ * the least loaded stream), forked from and joined back to the context's
+ * stream by events, so a capture of the context's stream (gbqr_graph_begin /
+ * gbqr_graph_end) turns the whole batch into one graph launch.  Each stream
+ * has its own workspace slice (gbqr_batched_workspace_bytes in total); the
+ * first call creates the streams and grows library-owned workspace, so make
+ * it before any capture.  opts apply to every matrix (panel_nb per matrix is
+ * min(opts->panel_nb or 128, n[i])).  Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_factor_batched(gbqr_ctx *ctx, int count, const int64_t *m, const int64_t *n,
+                                         double *const *A, const int64_t *lda, double *const *T,
+                                         const int64_t *ldt, const gbqr_opts *opts);
+
+/* Workspace bytes gbqr_factor_batched needs for these shapes (0 if invalid). */
+GBQR_API size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *n, const gbqr_opts *opts);
+
+typedef struct gbqr_graph gbqr_graph;
+
+/* Begin capturing the context's stream into a CUDA graph (relaxed capture
+ * mode).  Every library call until gbqr_graph_end is recorded, not run; the
+ * calls must not need new workspace or streams (make one uncaptured call
+ * first).  Tracing must be off.  Errors: EINVAL, EBUSY, ECUDA. */
+GBQR_API gbqr_status gbqr_graph_begin(gbqr_ctx *ctx);
+/* End the capture and instantiate it; *out receives the graph. */
+GBQR_API gbqr_status gbqr_graph_end(gbqr_ctx *ctx, gbqr_graph **out);
+/* Launch a captured graph on the context's stream (asynchronous). */
+GBQR_API gbqr_status gbqr_graph_launch(gbqr_ctx *ctx, gbqr_graph *g);
+GBQR_API gbqr_status gbqr_graph_destroy(gbqr_graph *g);
+
 /* ---- applying Q (basis-kernel update equation, Section 2.3) ------------ */
 
 /* B <- Q^T B for the m x nrhs matrix B, with Q = I - V T V^T given by the

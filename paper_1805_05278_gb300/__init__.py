@@ -65,6 +65,15 @@ SIGNATURES = {
     "gbqr_ls_solve": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _P, ctypes.c_int, ctypes.POINTER(gbqr_info)]),
     "gbqr_gemm_split_bf16": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, _I64, ctypes.c_double, _P, _I64, _P, _I64,
                                              ctypes.c_double, _P, _I64, ctypes.c_int]),
+    "gbqr_factor_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                            ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
+                                            ctypes.POINTER(_I64), ctypes.POINTER(gbqr_opts)]),
+    "gbqr_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                                       ctypes.POINTER(gbqr_opts)]),
+    "gbqr_graph_begin": (ctypes.c_int, [_P]),
+    "gbqr_graph_end": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
+    "gbqr_graph_launch": (ctypes.c_int, [_P, _P]),
+    "gbqr_graph_destroy": (ctypes.c_int, [_P]),
     "gbqr_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gbqr_trace_read": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_trace_rec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_launch_count": (_I64, [_P]),
@@ -264,12 +273,58 @@ class Context:
         return check(gbqr_gemm_split_bf16(self.handle, 1 if transa else 0, M, nc, K, alpha, _P(pa), lda,  # noqa: F821
                                           _P(pb), ldb, beta, _P(pc), ldc, nsplit), "gbqr_gemm_split_bf16")
 
+    def factor_batched(self, As, Ts, o: gbqr_opts | None = None) -> int:
+        """QR of every column-major matrix in As (in place); Ts[i] receives
+        the panel kernels (rows >= min(128, n_i))."""
+        cnt = len(As)
+        I64 = _I64 * cnt
+        Ps = _P * cnt
+        ms, ns, ldas, ldts, pa, pt = I64(), I64(), I64(), I64(), Ps(), Ps()
+        for i, (A, T) in enumerate(zip(As, Ts)):
+            a_ptr, m, n, lda = _cm(A, "A")
+            t_ptr, _, _, ldt = _cm(T, "T")
+            ms[i], ns[i], ldas[i], ldts[i], pa[i], pt[i] = m, n, lda, ldt, a_ptr, t_ptr
+        return check(gbqr_factor_batched(self.handle, cnt, ms, ns, pa, ldas, pt, ldts,  # noqa: F821
+                                         ctypes.byref(o) if o is not None else None), "gbqr_factor_batched")
+
+    def capture(self, fn):
+        """Run fn() under a capture of this context's stream; returns a Graph."""
+        check(gbqr_graph_begin(self.handle), "gbqr_graph_begin")  # noqa: F821
+        try:
+            fn()
+        finally:
+            g = _P()
+            st = gbqr_graph_end(self.handle, ctypes.byref(g))  # noqa: F821
+        check(st, "gbqr_graph_end")
+        return Graph(self, g)
+
     def ls_solve(self, A, b, x, prec: int = GBQR_FP64):
         pa, m, n, lda = _cm(A, "A")
         info = gbqr_info()
         st = gbqr_ls_solve(self.handle, m, n, _P(pa), lda, _P(b.data_ptr()), _P(x.data_ptr()), prec,  # noqa: F821
                            ctypes.byref(info))
         return st, info
+
+
+class Graph:
+    """A captured sequence of library calls (one CUDA graph launch)."""
+
+    def __init__(self, ctx, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def launch(self):
+        check(gbqr_graph_launch(self.ctx.handle, self.handle), "gbqr_graph_launch")  # noqa: F821
+
+    def close(self):
+        if self.handle:
+            gbqr_graph_destroy(self.handle)  # noqa: F821
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def workspace_bytes(m: int, n: int, layout: int = GBQR_T_PANEL, o: gbqr_opts | None = None) -> int:

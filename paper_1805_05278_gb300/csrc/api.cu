@@ -23,6 +23,7 @@ namespace {
 constexpr int kDefaultCutoff = 32;
 constexpr int kDefaultFanout = 0;   // 0: the TSQR planner chooses
 constexpr int64_t kDefaultPanel = 128;
+constexpr int kBatchLanes = 16;       // streams a batched factorization spreads over
 
 struct DeviceInfo {
     unsigned long long nonfinite;
@@ -108,7 +109,7 @@ struct Layout {
     TsqrPlan tsqr;
 };
 
-Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num_sms) {
+Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num_sms, bool staging = true) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 16), 256); return o; };
@@ -122,8 +123,8 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     nM = std::max(nM, (size_t)nb * (size_t)std::max<int64_t>(n, 1));
     if (t_layout == GBQR_T_FULL) nM = std::max(nM, (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1));
     L.n_M = nM;
-    L.n_bigA = (size_t)std::max<int64_t>(m, 1) * (size_t)std::max<int64_t>(n, 1);
-    L.n_bigT = (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1);
+    L.n_bigA = staging ? (size_t)std::max<int64_t>(m, 1) * (size_t)std::max<int64_t>(n, 1) : 1;
+    L.n_bigT = staging ? (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1) : 1;
     L.partial = take(L.n_partial * 8);
     L.counter_bytes = align_up(L.n_gcount * 4, 16) + L.tsqr.ncount * 4;
     L.gcount = take(L.counter_bytes);
@@ -136,7 +137,7 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     L.M2 = take(nM * 8);
     // second lane: panel factorizations of width <= nb run there
     L.n_Mb = std::max<size_t>((size_t)nb * (size_t)nb, 16);
-    L.partial2 = take(L.n_partial * 8);
+    L.partial2 = take(pr.lookahead ? L.n_partial * 8 : 16);
     L.gcount2 = take(align_up(L.n_gcount * 4, 16));
     L.M1b = take(L.n_Mb * 8);
     L.M2b = take(L.n_Mb * 8);
@@ -149,7 +150,7 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     L.bigA = take(L.n_bigA * 8);
     L.bigT = take(L.n_bigT * 8);
     // least squares: vectors f, r (m) and x, dx, g (n) of the refinement
-    L.vec = take(((size_t)3 * std::max<int64_t>(m, 1) + 4 * (size_t)std::max<int64_t>(n, 1) + 16) * 8);
+    L.vec = take(staging ? ((size_t)3 * std::max<int64_t>(m, 1) + 4 * (size_t)std::max<int64_t>(n, 1) + 16) * 8 : 16);
     L.total = off;
     return L;
 }
@@ -169,6 +170,8 @@ struct gbqr_ctx {
     bool tracing = false;
     cudaStream_t side = nullptr;          // high-priority stream for look-ahead panels
     cudaEvent_t ev_panel = nullptr, ev_ready = nullptr, ev_fork = nullptr;
+    std::vector<cudaStream_t> lanes;      // batched factorization: one stream per lane
+    std::vector<cudaEvent_t> lane_done;
 
     Exec exec() {
         Exec e;
@@ -217,6 +220,7 @@ gbqr_status ensure_workspace(gbqr_ctx *cx, size_t bytes) {
     if (cx->ws) {
         cudaStreamSynchronize(cx->stream);
         if (cx->side) cudaStreamSynchronize(cx->side);
+        for (auto st : cx->lanes) cudaStreamSynchronize(st);
         cudaFree(cx->ws);
         cx->ws = nullptr;
         cx->ws_bytes = 0;
@@ -228,15 +232,12 @@ gbqr_status ensure_workspace(gbqr_ctx *cx, size_t bytes) {
     return GBQR_OK;
 }
 
-gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const Params &pr, Work *w) {
-    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+// Point w's buffers into the workspace region at `base` laid out as L.
+void carve_work(gbqr_ctx *cx, char *base, const Layout &L, const Params &pr, const Exec &ex, Work *w) {
     w->cx = cx;
     w->pr = pr;
-    w->L = make_layout(m, n, t_layout, pr, cx->num_sms);
-    gbqr_status st = ensure_workspace(cx, w->L.total);
-    if (st != GBQR_OK) return st;
-    w->ex = cx->exec();
-    char *base = cx->ws;
+    w->L = L;
+    w->ex = ex;
     w->gs.partial = (double *)(base + w->L.partial);
     w->gs.partial_elems = w->L.n_partial;
     w->gs.counters = (unsigned *)(base + w->L.gcount);
@@ -253,7 +254,7 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
     w->vec = (double *)(base + w->L.vec);
     w->n_M = w->L.n_M;
     w->gs2.partial = (double *)(base + w->L.partial2);
-    w->gs2.partial_elems = w->L.n_partial;
+    w->gs2.partial_elems = pr.lookahead ? w->L.n_partial : 0;
     w->gs2.counters = (unsigned *)(base + w->L.gcount2);
     w->gs2.ncounters = w->L.n_gcount;
     w->M1b = (double *)(base + w->L.M1b);
@@ -261,12 +262,23 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
     w->tcs.base = w->L.n_tc ? (void *)(base + w->L.tc) : nullptr;
     w->tcs.bytes = w->L.n_tc;
     w->tcs.err = &cx->dinfo->timeout;
-    // arrival counters start at zero (every kernel leaves them zero again)
-    if (cudaMemsetAsync(base + w->L.gcount, 0, w->L.counter_bytes, cx->stream) != cudaSuccess)
-        return GBQR_ECUDA;
-    if (cudaMemsetAsync(base + w->L.gcount2, 0, align_up(w->L.n_gcount * 4, 16), cx->stream) != cudaSuccess)
-        return GBQR_ECUDA;
+}
+
+// Arrival counters start at zero (every kernel leaves them zero again).
+gbqr_status zero_counters(const Work &w, cudaStream_t s) {
+    char *base = (char *)w.gs.partial - w.L.partial;
+    if (cudaMemsetAsync(base + w.L.gcount, 0, w.L.counter_bytes, s) != cudaSuccess) return GBQR_ECUDA;
+    if (cudaMemsetAsync(base + w.L.gcount2, 0, align_up(w.L.n_gcount * 4, 16), s) != cudaSuccess) return GBQR_ECUDA;
     return GBQR_OK;
+}
+
+gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const Params &pr, Work *w) {
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    const Layout L = make_layout(m, n, t_layout, pr, cx->num_sms);
+    gbqr_status st = ensure_workspace(cx, L.total);
+    if (st != GBQR_OK) return st;
+    carve_work(cx, cx->ws, L, pr, cx->exec(), w);
+    return zero_counters(*w, cx->stream);
 }
 
 #define TRY(x) do { gbqr_status _s = (x); if (_s != GBQR_OK) return _s; } while (0)
@@ -558,6 +570,8 @@ gbqr_status gbqr_destroy(gbqr_ctx *cx) {
     if (cx->ev_ready) cudaEventDestroy(cx->ev_ready);
     if (cx->ev_fork) cudaEventDestroy(cx->ev_fork);
     if (cx->side) cudaStreamDestroy(cx->side);
+    for (auto st : cx->lanes) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    for (auto ev : cx->lane_done) cudaEventDestroy(ev);
     delete cx->tracer;
     delete cx;
     return GBQR_OK;
@@ -767,6 +781,138 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     }
     if (rk >= 0) return GBQR_ERANKDEF;
     return converged ? GBQR_OK : GBQR_ENOCONV;
+}
+
+gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, double *const *A,
+                                const int64_t *lda, double *const *T, const int64_t *ldt, const gbqr_opts *opts) {
+    if (!cx || count < 0) return GBQR_EINVAL;
+    if (count == 0) return GBQR_OK;
+    if (!m || !n || !A || !lda || !T || !ldt) return GBQR_EINVAL;
+    int64_t mmax = 1, nmax = 1;
+    std::vector<double> cost(count);
+    for (int i = 0; i < count; ++i) {
+        Params pi;
+        if (!resolve(opts, m[i], n[i], &pi)) return GBQR_EINVAL;
+        TRY(check_layout_args(m[i], n[i], lda[i], ldt[i], GBQR_T_PANEL, pi.nb));
+        if (n[i] > 0 && (!A[i] || !T[i])) return GBQR_EINVAL;
+        mmax = std::max(mmax, m[i]);
+        nmax = std::max(nmax, n[i]);
+        cost[i] = 2.0 * m[i] * (double)n[i] * n[i] - 2.0 * (double)n[i] * n[i] * n[i] / 3.0 + 1e5 * n[i];
+    }
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    Params pr;
+    if (!resolve(opts, mmax, nmax, &pr)) return GBQR_EINVAL;
+    pr.lookahead = false;                       // one stream per lane
+    const int S = std::min(count, kBatchLanes);
+    const int lane_sms = std::max(8, (2 * cx->num_sms + S - 1) / S);
+    const Layout L = make_layout(mmax, nmax, GBQR_T_PANEL, pr, lane_sms, /*staging=*/false);
+    const size_t lane_bytes = align_up(L.total, 256);
+    TRY(ensure_workspace(cx, lane_bytes * S));
+    // lane streams and their completion events (created on first use: make
+    // the first batched call before any stream capture)
+    while ((int)cx->lanes.size() < S) {
+        cudaStream_t st;
+        cudaEvent_t ev;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return GBQR_ECUDA;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) { cudaStreamDestroy(st); return GBQR_ECUDA; }
+        cx->lanes.push_back(st);
+        cx->lane_done.push_back(ev);
+    }
+    // largest problems first, each to the least loaded lane
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<std::vector<int>> work(S);
+    std::vector<double> load(S, 0.0);
+    for (int i : order) {
+        const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        work[l].push_back(i);
+        load[l] += cost[i];
+    }
+    // fork from the context stream, one lane per stream, join back
+    if (cudaEventRecord(cx->ev_fork, cx->stream) != cudaSuccess) return GBQR_ECUDA;
+    for (int l = 0; l < S; ++l) {
+        if (cudaStreamWaitEvent(cx->lanes[l], cx->ev_fork, 0) != cudaSuccess) return GBQR_ECUDA;
+        Exec ex = cx->exec();
+        ex.stream = cx->lanes[l];
+        ex.num_sms = lane_sms;
+        Work w;
+        carve_work(cx, cx->ws + lane_bytes * l, L, pr, ex, &w);
+        TRY(zero_counters(w, ex.stream));
+        for (int i : work[l]) {
+            if (n[i] == 0) continue;
+            Params pi;
+            resolve(opts, m[i], n[i], &pi);
+            w.pr.nb = pi.nb;
+            TRY(factor_device(w, m[i], n[i], A[i], lda[i], T[i], ldt[i], GBQR_T_PANEL));
+        }
+        if (cudaEventRecord(cx->lane_done[l], ex.stream) != cudaSuccess) return GBQR_ECUDA;
+        if (cudaStreamWaitEvent(cx->stream, cx->lane_done[l], 0) != cudaSuccess) return GBQR_ECUDA;
+    }
+    return GBQR_OK;
+}
+
+size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *n, const gbqr_opts *opts) {
+    if (count <= 0 || !m || !n) return 0;
+    int64_t mmax = 1, nmax = 1;
+    for (int i = 0; i < count; ++i) {
+        if (m[i] < n[i] || n[i] < 0) return 0;
+        mmax = std::max(mmax, m[i]);
+        nmax = std::max(nmax, n[i]);
+    }
+    Params pr;
+    if (!resolve(opts, mmax, nmax, &pr)) return 0;
+    pr.lookahead = false;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    const int S = std::min(count, kBatchLanes);
+    const int lane_sms = std::max(8, (2 * sms + S - 1) / S);
+    return align_up(make_layout(mmax, nmax, GBQR_T_PANEL, pr, lane_sms, false).total, 256) * S;
+}
+
+struct gbqr_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+gbqr_status gbqr_graph_begin(gbqr_ctx *cx) {
+    if (!cx) return GBQR_EINVAL;
+    if (cx->tracing) return GBQR_EBUSY;
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    return cudaStreamBeginCapture(cx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+}
+
+gbqr_status gbqr_graph_end(gbqr_ctx *cx, gbqr_graph **out) {
+    if (!cx || !out) return GBQR_EINVAL;
+    *out = nullptr;
+    gbqr_graph *g = new (std::nothrow) gbqr_graph();
+    if (!g) return GBQR_ENOMEM;
+    if (cudaStreamEndCapture(cx->stream, &g->graph) != cudaSuccess ||
+        cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return GBQR_ECUDA;
+    }
+    *out = g;
+    return GBQR_OK;
+}
+
+gbqr_status gbqr_graph_launch(gbqr_ctx *cx, gbqr_graph *g) {
+    if (!cx || !g) return GBQR_EINVAL;
+    if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    return cudaGraphLaunch(g->exec, cx->stream) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+}
+
+gbqr_status gbqr_graph_destroy(gbqr_graph *g) {
+    if (!g) return GBQR_EINVAL;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+    return GBQR_OK;
 }
 
 gbqr_status gbqr_trace_enable(gbqr_ctx *cx, int on) {

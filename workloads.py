@@ -129,3 +129,33 @@ WORKLOADS = {w.name: w for w in (SMALL_1024x128, TALL_32768x2048, SQUARE_8192)}
 
 def log_uniform_int(rng: np.random.Generator, lo: int, hi: int) -> int:
     return int(math.floor(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+
+def batched_shapes(count: int = 2000, seed: int = 20, m_range=(256, 16384), n_range=(16, 256)):
+    """Shapes of the batched tall-skinny workload: m log-uniform in m_range,
+    n uniform in n_range (inclusive), n <= m (resampled otherwise)."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    while len(shapes) < count:
+        m = log_uniform_int(rng, *m_range)
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        if n <= m:
+            shapes.append((m, n))
+    return shapes
+
+
+def batched_device_buffer(shapes, seed: int, device="cuda"):
+    """All matrices of a batch in one contiguous float64 device buffer (iid
+    N(0,1) from a seeded torch generator); returns (buffer, offsets): matrix
+    i is column-major m_i x n_i starting at offsets[i] with ld = m_i."""
+    import torch
+    sizes = [m * n for (m, n) in shapes]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    buf = torch.randn(int(offsets[-1]), dtype=torch.float64, device=device, generator=gen)
+    return buf, offsets[:-1]
+
+
+# The batched workload: 2000 tall-skinny matrices.
+BATCHED_SEED = 20
