@@ -65,6 +65,8 @@ def parse():
     p.add_argument("--ls-decades", type=float, default=4.0)
     p.add_argument("--batched", type=int, default=2000, help="matrices in the batched measurement (0: skip)")
     p.add_argument("--batched-steps", type=int, default=3)
+    p.add_argument("--batched-streams", type=int, default=0)
+    p.add_argument("--batched-cutoff", type=int, default=0)
     return p.parse_args()
 
 
@@ -82,10 +84,11 @@ def measure_batched(gb, dev, args):
     stream = torch.cuda.Stream(dev)
     ctx = gb.Context(dev, stream)
     flops = sum(workloads.qr_flops(m, n) for (m, n) in shapes)
+    o = gb.opts(batch_streams=args.batched_streams, cutoff_b=args.batched_cutoff)
     with torch.cuda.stream(stream):
-        ctx.factor_batched(As, Ts)                      # warm-up: lanes, workspace
+        ctx.factor_batched(As, Ts, o)                   # warm-up: lanes, workspace
         torch.cuda.synchronize()
-        graph = ctx.capture(lambda: ctx.factor_batched(As, Ts))
+        graph = ctx.capture(lambda: ctx.factor_batched(As, Ts, o))
         launches0 = ctx.launch_count()
         times = []
         for _ in range(max(1, args.batched_steps)):
@@ -102,7 +105,8 @@ def measure_batched(gb, dev, args):
     ms = sorted(times)[len(times) // 2]
     return {"workload": f"{len(shapes)} FP64 matrices, m log-uniform [256, 16384], n uniform [16, 256], seed {workloads.BATCHED_SEED}",
             "total_flops": flops, "ms_per_batch": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-            "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st)}
+            "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st),
+            "streams": args.batched_streams or 128, "cutoff_b": args.batched_cutoff or 16}
 
 
 def measure_ls(gb, ctx, dev, args):

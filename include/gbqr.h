@@ -98,7 +98,8 @@ typedef struct {
                            GBQR_MIXED_SPLITBF16 (three slices, FP32-level) on
                            the tensor cores.  Reflector generation, the TSQR
                            R-merges and the in-panel products stay FP64. */
-    int32_t reserved[2];
+    int32_t batch_streams; /* gbqr_factor_batched: streams to spread over (1..128) */
+    int32_t reserved[1];
 } gbqr_opts;
 
 /* Device-side record of one or more calls since the last gbqr_sync(). */
@@ -181,14 +182,15 @@ GBQR_API int64_t gbqr_default_panel_nb(int64_t m, int64_t n);
  * for each matrix): A[i] (m[i] x n[i], lda[i], device) is factored in place
  * exactly as gbqr_factor does with GBQR_T_PANEL, T[i] (ldt[i] x n[i]) receives
  * its panel kernels.  m, n, A, lda, T, ldt are HOST arrays of count entries.
- * The matrices are spread over up to 16 internal streams (largest first, to
+ * The matrices are spread over opts->batch_streams (default 128) internal streams (largest first, to
  * the least loaded stream), forked from and joined back to the context's
  * stream by events, so a capture of the context's stream (gbqr_graph_begin /
  * gbqr_graph_end) turns the whole batch into one graph launch.  Each stream
  * has its own workspace slice (gbqr_batched_workspace_bytes in total); the
  * first call creates the streams and grows library-owned workspace, so make
  * it before any capture.  opts apply to every matrix (panel_nb per matrix is
- * min(opts->panel_nb or 128, n[i])).  Errors: EINVAL, ENOMEM, ECUDA. */
+ * min(opts->panel_nb or 128, n[i]); the cutoff b defaults to 16 here).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
 GBQR_API gbqr_status gbqr_factor_batched(gbqr_ctx *ctx, int count, const int64_t *m, const int64_t *n,
                                          double *const *A, const int64_t *lda, double *const *T,
                                          const int64_t *ldt, const gbqr_opts *opts);

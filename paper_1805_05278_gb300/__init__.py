@@ -35,7 +35,8 @@ _P = ctypes.c_void_p
 class gbqr_opts(ctypes.Structure):
     _fields_ = [("cutoff_b", ctypes.c_int32), ("panel_nb", ctypes.c_int32),
                 ("leaf_rows", ctypes.c_int32), ("fanout", ctypes.c_int32),
-                ("lookahead", ctypes.c_int32), ("update_prec", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("lookahead", ctypes.c_int32), ("update_prec", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class gbqr_info(ctypes.Structure):
@@ -127,11 +128,12 @@ def check(status: int, what: str) -> int:
 
 
 def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int = 0,
-         lookahead: int = 0, update_prec: int = GBQR_FP64) -> gbqr_opts:
+         lookahead: int = 0, update_prec: int = GBQR_FP64, batch_streams: int = 0) -> gbqr_opts:
     o = gbqr_opts()
     o.cutoff_b, o.panel_nb, o.leaf_rows, o.fanout = cutoff_b, panel_nb, leaf_rows, fanout
     o.lookahead = lookahead
     o.update_prec = update_prec
+    o.batch_streams = batch_streams
     return o
 
 

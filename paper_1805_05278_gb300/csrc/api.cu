@@ -23,7 +23,9 @@ namespace {
 constexpr int kDefaultCutoff = 32;
 constexpr int kDefaultFanout = 0;   // 0: the TSQR planner chooses
 constexpr int64_t kDefaultPanel = 128;
-constexpr int kBatchLanes = 16;       // streams a batched factorization spreads over
+constexpr int kBatchLanes = 128;      // streams a batched factorization spreads over (measured best of 16..128)
+constexpr int kBatchCutoff = 16;      // batched default cutoff b (measured best of 16, 32)
+constexpr int kMaxBatchLanes = 128;
 
 struct DeviceInfo {
     unsigned long long nonfinite;
@@ -88,6 +90,7 @@ bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
         if (o->leaf_rows) r.leaf_rows = o->leaf_rows;
         if (o->fanout) r.fanout = o->fanout;
         if (o->lookahead < -1 || o->lookahead > 1) return false;
+        if (o->batch_streams < 0) return false;
         if (o->lookahead == -1) r.lookahead = false;
         if (o->update_prec == GBQR_MIXED_BF16) r.nsplit = 1;
         else if (o->update_prec == GBQR_MIXED_SPLITBF16) r.nsplit = 3;
@@ -803,7 +806,8 @@ gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const
     Params pr;
     if (!resolve(opts, mmax, nmax, &pr)) return GBQR_EINVAL;
     pr.lookahead = false;                       // one stream per lane
-    const int S = std::min(count, kBatchLanes);
+    if (!opts || opts->cutoff_b == 0) pr.b = kBatchCutoff;
+    const int S = std::min(count, opts && opts->batch_streams > 0 ? std::min(opts->batch_streams, kMaxBatchLanes) : kBatchLanes);
     const int lane_sms = std::max(8, (2 * cx->num_sms + S - 1) / S);
     const Layout L = make_layout(mmax, nmax, GBQR_T_PANEL, pr, lane_sms, /*staging=*/false);
     const size_t lane_bytes = align_up(L.total, 256);
@@ -843,7 +847,7 @@ gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const
             if (n[i] == 0) continue;
             Params pi;
             resolve(opts, m[i], n[i], &pi);
-            w.pr.nb = pi.nb;
+            w.pr.nb = pi.nb;   // the cutoff stays the batch's (pr.b)
             TRY(factor_device(w, m[i], n[i], A[i], lda[i], T[i], ldt[i], GBQR_T_PANEL));
         }
         if (cudaEventRecord(cx->lane_done[l], ex.stream) != cudaSuccess) return GBQR_ECUDA;
@@ -863,12 +867,13 @@ size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *
     Params pr;
     if (!resolve(opts, mmax, nmax, &pr)) return 0;
     pr.lookahead = false;
+    if (!opts || opts->cutoff_b == 0) pr.b = kBatchCutoff;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         sms = 152;
     }
-    const int S = std::min(count, kBatchLanes);
+    const int S = std::min(count, opts && opts->batch_streams > 0 ? std::min(opts->batch_streams, kMaxBatchLanes) : kBatchLanes);
     const int lane_sms = std::max(8, (2 * sms + S - 1) / S);
     return align_up(make_layout(mmax, nmax, GBQR_T_PANEL, pr, lane_sms, false).total, 256) * S;
 }
