@@ -67,7 +67,61 @@ def parse():
     p.add_argument("--batched-steps", type=int, default=3)
     p.add_argument("--batched-streams", type=int, default=0)
     p.add_argument("--batched-cutoff", type=int, default=0)
+    p.add_argument("--serving", type=int, default=200, help="requests per serving run (0: skip)")
+    p.add_argument("--serving-rates", default="100,400,1600")
+    p.add_argument("--serving-workers", type=int, default=16)
     return p.parse_args()
+
+
+def measure_serving(gb, dev, args):
+    """Least-squares serving: Poisson arrivals at each rate, requests from
+    workloads.serving_specs, served by gbqr_server_* (continuous batching,
+    HBM admission cap 120 GB) with FP64 only vs GBQR_PREC_AUTO (mixed first,
+    FP64 when refinement stalls).  Reports solves/s (requests / makespan) and
+    p50 / p99 latency (submit to done) per rate and mode."""
+    import torch
+    specs = workloads.serving_specs(args.serving)
+    probs = [workloads.serving_device_problem(m, n, d, workloads.SERVING_SEED * 1000 + i, f"cuda:{dev}")
+             for i, (m, n, d) in enumerate(specs)]
+    xs = [torch.zeros(n, dtype=torch.float64, device=f"cuda:{dev}") for (m, n, d) in specs]
+    torch.cuda.synchronize()
+    rates = [float(r) for r in args.serving_rates.split(",") if r]
+    rng = np.random.default_rng(workloads.SERVING_SEED + 1)
+    gaps = rng.exponential(1.0, size=len(specs))
+    out = {"workload": f"{len(specs)} LS requests, m log-U[512,65536], n log-U[32,1024], kappa log-U[1e1,1e8], "
+                       f"one RHS, seed {workloads.SERVING_SEED}", "workers": args.serving_workers,
+           "cap_bytes": 120 << 30, "mean_flops_per_request": float(np.mean([2.0 * m * n * n for (m, n, d) in specs]))}
+    for mode, prec in [("fp64", gb.GBQR_FP64), ("mixed_auto", gb.GBQR_PREC_AUTO)]:
+        ctx = gb.Context(dev)
+        ctx.serve(args.serving_workers, 120 << 30)
+        # warm-up: one request of each size class through the server
+        for i in range(min(4, len(specs))):
+            ctx.poll(ctx.submit(probs[i][0], probs[i][2], xs[i], prec), wait=True)
+        res_mode = {}
+        for rate in rates:
+            arrivals = np.cumsum(gaps / rate)
+            t0 = time.perf_counter()
+            ids = []
+            for i, (a, xt, b) in enumerate(probs):
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:
+                    time.sleep(arrivals[i] - now)
+                ids.append(ctx.submit(a, b, xs[i], prec, tag=i))
+            results = [ctx.poll(r, wait=True) for r in ids]
+            makespan = max(r.latency_ms / 1e3 + arrivals[i] for i, r in enumerate(results))
+            lat = sorted(r.latency_ms for r in results)
+            bad = sum(1 for r in results if r.status != gb.GBQR_OK)
+            fell_back = sum(1 for r in results if prec == gb.GBQR_PREC_AUTO and r.prec_used == gb.GBQR_FP64)
+            res_mode[str(int(rate))] = {"solves_per_s": len(results) / makespan,
+                                        "p50_ms": lat[len(lat) // 2],
+                                        "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                                        "failed": bad, "fp64_fallbacks": fell_back}
+        errs = [float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, (a, xt, b) in zip(xs, probs)]
+        res_mode["max_rel_err_vs_xtrue"] = max(errs)
+        ctx.stop_serving()
+        ctx.close()
+        out[mode] = res_mode
+    return out
 
 
 def measure_batched(gb, dev, args):
@@ -368,6 +422,7 @@ def run_gbqr(args):
     st, info = ctx.sync()
     ls = measure_ls(gb, None, dev, args) if (args.ls_solves > 0 and rank == 0) else None
     batched = measure_batched(gb, dev, args) if (args.batched > 0 and rank == 0) else None
+    serving = measure_serving(gb, dev, args) if (args.serving > 0 and rank == 0) else None
 
     gemm = trace.get("gemm", {})
     achieved = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm.get("ms") else None
@@ -408,6 +463,7 @@ def run_gbqr(args):
             "cpu_baseline": cpu,
             "ls": ls,
             "batched": batched,
+            "serving": serving,
             "status_after": int(st),
         }
         print(json.dumps(line), flush=True)

@@ -79,7 +79,8 @@ typedef enum {
     GBQR_FP64 = 0,          /* every step in FP64 */
     GBQR_MIXED_BF16 = 1,    /* reserved: tensor-core update GEMMs + refinement */
     GBQR_MIXED_SPLITBF16 = 2,
-    GBQR_FP32 = 3
+    GBQR_FP32 = 3,
+    GBQR_PREC_AUTO = 4      /* serving: mixed first, FP64 when refinement stalls */
 } gbqr_prec;
 
 /* Algorithm parameters.  Zero selects the library's tuned default. */
@@ -270,6 +271,55 @@ GBQR_API gbqr_status gbqr_ls_solve(gbqr_ctx *ctx, int64_t m, int64_t n, const do
 GBQR_API gbqr_status gbqr_gemm_split_bf16(gbqr_ctx *ctx, int transa, int64_t M, int64_t N, int64_t K,
                                           double alpha, const double *A, int64_t lda, const double *B,
                                           int64_t ldb, double beta, double *C, int64_t ldc, int nsplit);
+
+/* ---- serving: least squares with continuous batching -------------------- */
+
+typedef enum { GBQR_REQ_QUEUED = 0, GBQR_REQ_RUNNING = 1, GBQR_REQ_DONE = 2 } gbqr_req_state;
+
+typedef struct {
+    int64_t m, n;          /* problem size, m >= n >= 1 */
+    const double *A;       /* device, m x n column-major (lda >= m), not modified */
+    int64_t lda;
+    const double *b;       /* device, m entries */
+    double *x;             /* device, n entries: the solution */
+    int32_t prec;          /* GBQR_FP64, GBQR_MIXED_*, or GBQR_PREC_AUTO */
+    int32_t pad;
+    uint64_t tag;          /* caller's label, echoed in the result */
+} gbqr_request;
+
+typedef struct {
+    int32_t state;         /* gbqr_req_state */
+    int32_t status;        /* gbqr_status of the solve (when done) */
+    int32_t prec_used;     /* the precision that produced x */
+    int32_t pad;
+    int64_t refine_iters;
+    double queue_ms;       /* submit -> admitted */
+    double run_ms;         /* admitted -> done */
+    double latency_ms;     /* submit -> done */
+    int64_t footprint_bytes;
+    uint64_t tag;
+} gbqr_result;
+
+/* Start a serving loop on `device` attached to ctx: `workers` host threads,
+ * each with a private context and stream, so admitted requests overlap on
+ * the device; at most mem_cap_bytes of workspace in flight.  A queued request
+ * is admitted (first fit, in arrival order) when a worker is free and its
+ * workspace footprint - gbqr_workspace_bytes of its shape and precision -
+ * fits under the cap beside the running ones; its workspace comes from the
+ * stream-ordered allocator and returns on completion.  Each request runs
+ * gbqr_ls_solve (Section 2.1 least squares through the QR); the kernels are
+ * deterministic, so a result does not depend on what else is in flight.
+ * Errors: EINVAL, EBUSY (already started), ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_server_start(gbqr_ctx *ctx, int device, int workers, size_t mem_cap_bytes);
+/* Queue a request; *id receives its handle.  The request's buffers must stay
+ * valid until it is done.  Errors: EINVAL, ENOMEM (footprint above the cap),
+ * EBUSY (stopping). */
+GBQR_API gbqr_status gbqr_submit(gbqr_ctx *ctx, const gbqr_request *req, uint64_t *id);
+/* State of request id; wait != 0 blocks until it is done.  A done result is
+ * returned once and then forgotten.  Errors: EINVAL (unknown id). */
+GBQR_API gbqr_status gbqr_poll(gbqr_ctx *ctx, uint64_t id, int wait, gbqr_result *out);
+/* Serve what is queued, then stop the workers. */
+GBQR_API gbqr_status gbqr_server_stop(gbqr_ctx *ctx);
 
 /* ---- tracing ------------------------------------------------------------ */
 

@@ -26,7 +26,8 @@ GBQR_OK, GBQR_EINVAL, GBQR_ENOMEM, GBQR_ECUDA, GBQR_ETIMEOUT = 0, 1, 2, 3, 4
 GBQR_ENONFINITE, GBQR_ERANKDEF, GBQR_EBUSY, GBQR_EUNSUPPORTED, GBQR_ENOCONV = 5, 6, 7, 8, 9
 # T layouts (gbqr_t_layout) and precisions (gbqr_prec)
 GBQR_T_FULL, GBQR_T_PANEL = 0, 1
-GBQR_FP64, GBQR_MIXED_BF16, GBQR_MIXED_SPLITBF16, GBQR_FP32 = 0, 1, 2, 3
+GBQR_FP64, GBQR_MIXED_BF16, GBQR_MIXED_SPLITBF16, GBQR_FP32, GBQR_PREC_AUTO = 0, 1, 2, 3, 4
+GBQR_REQ_QUEUED, GBQR_REQ_RUNNING, GBQR_REQ_DONE = 0, 1, 2
 
 _I64 = ctypes.c_int64
 _P = ctypes.c_void_p
@@ -43,6 +44,19 @@ class gbqr_info(ctypes.Structure):
     _fields_ = [("nonfinite", ctypes.c_int64), ("zero_pivots", ctypes.c_int64),
                 ("rankdef_col", ctypes.c_int64), ("refine_iters", ctypes.c_int64),
                 ("refine_last", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
+
+
+class gbqr_request(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("b", ctypes.c_void_p), ("x", ctypes.c_void_p), ("prec", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("tag", ctypes.c_uint64)]
+
+
+class gbqr_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("prec_used", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("refine_iters", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
+                ("tag", ctypes.c_uint64)]
 
 
 class gbqr_trace_rec(ctypes.Structure):
@@ -75,6 +89,10 @@ SIGNATURES = {
     "gbqr_graph_end": (ctypes.c_int, [_P, ctypes.POINTER(_P)]),
     "gbqr_graph_launch": (ctypes.c_int, [_P, _P]),
     "gbqr_graph_destroy": (ctypes.c_int, [_P]),
+    "gbqr_server_start": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_size_t]),
+    "gbqr_submit": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "gbqr_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(gbqr_result)]),
+    "gbqr_server_stop": (ctypes.c_int, [_P]),
     "gbqr_trace_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "gbqr_trace_read": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_trace_rec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_launch_count": (_I64, [_P]),
@@ -299,6 +317,25 @@ class Context:
             st = gbqr_graph_end(self.handle, ctypes.byref(g))  # noqa: F821
         check(st, "gbqr_graph_end")
         return Graph(self, g)
+
+    # ---- serving
+    def serve(self, workers: int = 16, mem_cap_bytes: int = 120 << 30):
+        check(gbqr_server_start(self.handle, self.device, workers, mem_cap_bytes), "gbqr_server_start")  # noqa: F821
+
+    def submit(self, A, b, x, prec: int = GBQR_PREC_AUTO, tag: int = 0) -> int:
+        pa, m, n, lda = _cm(A, "A")
+        r = gbqr_request(m=m, n=n, A=pa, lda=lda, b=b.data_ptr(), x=x.data_ptr(), prec=prec, pad=0, tag=tag)
+        rid = ctypes.c_uint64(0)
+        check(gbqr_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)), "gbqr_submit")  # noqa: F821
+        return rid.value
+
+    def poll(self, rid: int, wait: bool = False) -> gbqr_result:
+        out = gbqr_result()
+        check(gbqr_poll(self.handle, rid, 1 if wait else 0, ctypes.byref(out)), "gbqr_poll")  # noqa: F821
+        return out
+
+    def stop_serving(self):
+        return gbqr_server_stop(self.handle)  # noqa: F821
 
     def ls_solve(self, A, b, x, prec: int = GBQR_FP64):
         pa, m, n, lda = _cm(A, "A")

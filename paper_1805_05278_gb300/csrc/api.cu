@@ -563,6 +563,7 @@ gbqr_status gbqr_create(gbqr_ctx **out, int device, void *cuda_stream) {
 
 gbqr_status gbqr_destroy(gbqr_ctx *cx) {
     if (!cx) return GBQR_EINVAL;
+    gbqr_server_stop(cx);   // a serving loop attached to this context, if any
     cudaSetDevice(cx->device);
     cudaStreamSynchronize(cx->stream);
     if (cx->side) cudaStreamSynchronize(cx->side);

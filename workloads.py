@@ -159,3 +159,34 @@ def batched_device_buffer(shapes, seed: int, device="cuda"):
 
 # The batched workload: 2000 tall-skinny matrices.
 BATCHED_SEED = 20
+SERVING_SEED = 30
+
+
+def serving_specs(count: int, seed: int = SERVING_SEED, m_range=(512, 65536), n_range=(32, 1024),
+                  kappa_range=(1e1, 1e8)):
+    """Least-squares requests of the serving workload: m, n log-uniform
+    (n <= m, resampled otherwise), target condition number log-uniform, set
+    by grading the columns of a Gaussian matrix over log10(kappa) decades."""
+    rng = np.random.default_rng(seed)
+    specs = []
+    while len(specs) < count:
+        m = log_uniform_int(rng, *m_range)
+        n = log_uniform_int(rng, *n_range)
+        if n > m:
+            continue
+        kappa = math.exp(rng.uniform(math.log(kappa_range[0]), math.log(kappa_range[1])))
+        specs.append((m, n, math.log10(kappa)))
+    return specs
+
+
+def serving_device_problem(m: int, n: int, decades: float, seed: int, device="cuda", noise: float = 1e-8):
+    """(A, x_true, b) on the device: A Gaussian with column j scaled by
+    10**(-decades*j/n), b = A x_true + noise N(0,1); seeded torch generator."""
+    import torch
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    a = torch.randn((n, m), dtype=torch.float64, device=device, generator=gen).T
+    a *= torch.from_numpy(column_scales(n, decades)).to(device)[None, :]
+    xt = torch.randn(n, dtype=torch.float64, device=device, generator=gen)
+    b = a @ xt + noise * torch.randn(m, dtype=torch.float64, device=device, generator=gen)
+    return a, xt, b
