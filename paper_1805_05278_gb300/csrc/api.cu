@@ -769,7 +769,7 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
             last = (hn[1] > 0.0) ? std::sqrt(hn[0] / hn[1]) : 0.0;
             if (!(last == last)) break;                                   // NaN: stop
             if (last <= 1e-16) { converged = true; break; }
-            if (iters >= 3 && last > 0.5 * prev) { converged = last <= 1e-12; break; }
+            if (iters >= 2 && last > 0.5 * prev) { converged = last <= 1e-12; break; }
             prev = last;
         }
     }

@@ -10,8 +10,10 @@
 // workspace comes from the stream-ordered allocator and is returned when it
 // completes, so memory freed by one request admits the next.
 //
-// GBQR_PREC_AUTO requests run the mixed path first (tensor-core updates +
-// FP64 refinement) and fall back to FP64 when the refinement stalls.
+// GBQR_PREC_AUTO requests run the mixed path (tensor-core updates + FP64
+// refinement) when the update GEMMs dominate their cost, FP64 otherwise, and
+// fall back to FP64 when the refinement stalls (condition number beyond
+// what FP32-level updates can refine).
 #include "common.cuh"
 
 #include <chrono>
@@ -36,6 +38,14 @@ struct Record {
     int64_t iters = 0;
     Clock::time_point t_submit, t_start, t_done;
 };
+
+// GBQR_PREC_AUTO: the tensor-core updates only pay off where the trailing
+// update GEMMs dominate (at least three 128-wide panels and m n^2 >= 4e9);
+// smaller problems are bound by the FP64 panel factorizations, where the
+// mixed path would only add refinement steps.
+int auto_precision(int64_t m, int64_t n) {
+    return (n > 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
+}
 
 size_t footprint_of(const gbqr_request &r, int prec) {
     gbqr_opts o;
@@ -105,7 +115,7 @@ void worker_loop(gbqr_server *sv, int wi) {
         } else {
             gbqr_set_workspace(cx, ws, rec->footprint);
             gbqr_info info;
-            const int first = (r.prec == GBQR_PREC_AUTO) ? GBQR_MIXED_SPLITBF16 : r.prec;
+            const int first = (r.prec == GBQR_PREC_AUTO) ? auto_precision(r.m, r.n) : r.prec;
             used = first;
             status = gbqr_ls_solve(cx, r.m, r.n, r.A, r.lda, r.b, r.x, first, &info);
             iters = info.refine_iters;
@@ -197,7 +207,7 @@ GBQR_API gbqr_status gbqr_submit(gbqr_ctx *ctx, const gbqr_request *req, uint64_
         return GBQR_EINVAL;
     Record rec;
     rec.req = r;
-    rec.footprint = footprint_of(r, r.prec == GBQR_PREC_AUTO ? GBQR_MIXED_SPLITBF16 : r.prec);
+    rec.footprint = footprint_of(r, r.prec == GBQR_PREC_AUTO ? auto_precision(r.m, r.n) : r.prec);
     if (rec.footprint > sv->cap) return GBQR_ENOMEM;
     rec.t_submit = Clock::now();
     {

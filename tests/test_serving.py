@@ -48,7 +48,8 @@ def _serve(gb, problems, precs, workers=8, cap=8 << 30):
 
 def test_mixed_stream_of_requests(gb, orc):
     problems = _requests(20, 7)
-    precs = [gb.GBQR_PREC_AUTO if i % 2 else gb.GBQR_FP64 for i in range(len(problems))]
+    cycle = [gb.GBQR_FP64, gb.GBQR_PREC_AUTO, gb.GBQR_MIXED_SPLITBF16]
+    precs = [cycle[i % 3] for i in range(len(problems))]
     results, xs = _serve(gb, problems, precs)
     for (a, b), r, x in zip(problems, results, xs):
         assert r.state == gb.GBQR_REQ_DONE and r.status == gb.GBQR_OK, (r.status, a.shape)
@@ -56,8 +57,9 @@ def test_mixed_stream_of_requests(gb, orc):
         kappa = np.linalg.cond(a)
         assert np.linalg.norm(x - x_o) / np.linalg.norm(x_o) <= max(1e-12, 50 * kappa * np.finfo(float).eps)
         assert r.latency_ms >= r.run_ms >= 0.0
+    assert any(r.prec_used == gb.GBQR_MIXED_SPLITBF16 for r in results)
     # alone vs in the mix: identical bits
-    for k in (0, 3, 8):
+    for k in (0, 2, 4, 8):
         alone, xa = _serve(gb, [problems[k]], [precs[k]], workers=1)
         assert np.array_equal(xa[0], xs[k]), k
         assert alone[0].prec_used == results[k].prec_used
