@@ -450,7 +450,7 @@ def run_gbqr(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed,
                        "t_layout": args.layout, "panel_nb": nb if layout == gb.GBQR_T_PANEL else None,
-                       "cutoff_b": args.cutoff or 32, "parallelism": f"replicas x{world}",
+                       "cutoff_b": args.cutoff or 16, "parallelism": f"replicas x{world}",
                        "l2": "inputs (%.0f MB) larger than L2, no flush" % (w.m * w.n * 8 / 1e6),
                        "step": "restore A from a device copy + gbqr_factor"},
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": w.m * w.n * 8,

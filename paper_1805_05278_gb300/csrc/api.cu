@@ -20,7 +20,7 @@ using namespace gbqr;
 
 namespace {
 
-constexpr int kDefaultCutoff = 32;
+constexpr int kDefaultCutoff = 16;   // measured best of 8, 16, 32 (FP64 and mixed)
 constexpr int kDefaultFanout = 0;   // 0: the TSQR planner chooses
 constexpr int64_t kDefaultPanel = 128;
 constexpr int kBatchLanes = 128;      // streams a batched factorization spreads over (measured best of 16..128)

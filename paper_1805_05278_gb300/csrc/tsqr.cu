@@ -586,9 +586,11 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 4 * (size_t)w * w - 2 * w) / w));   // recon
     if (hcap < w) return false;
     // default: about one leaf per SM (the leaf phase is the only one that
-    // uses the whole GPU), never shorter than the panel is wide
+    // uses the whole GPU), but at least 128 rows - shorter panels then get
+    // fewer leaves and one merge level less, which measured faster - and
+    // never shorter than the panel is wide
     const int sms = num_sms > 0 ? num_sms : 152;
-    int64_t target = leaf_rows > 0 ? leaf_rows : std::max<int64_t>(w, (mp + sms - 1) / sms);
+    int64_t target = leaf_rows > 0 ? leaf_rows : std::max<int64_t>({(int64_t)w, (int64_t)128, (mp + sms - 1) / sms});
     target = std::max<int64_t>(target, w);
     int64_t P = (mp + target - 1) / target;
     P = std::max<int64_t>(P, (mp + hcap - 1) / hcap);   // leaves no taller than hcap
