@@ -58,6 +58,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cutoff", type=int, default=0)
+    p.add_argument("--fp64-gemm", choices=["dmma", "dfma"], default="dfma",
+                   help="engine of the 64 x 64 FP64 GEMM tiles")
     p.add_argument("--panel", type=int, default=0)
     p.add_argument("--leaf", type=int, default=0)
     p.add_argument("--fanout", type=int, default=0)
@@ -356,7 +358,8 @@ def run_gbqr(args):
     gb.build()
     w = workloads.WORKLOADS[args.workload]
     layout = gb.GBQR_T_PANEL if args.layout == "panel" else gb.GBQR_T_FULL
-    o = gb.opts(cutoff_b=args.cutoff, panel_nb=args.panel, leaf_rows=args.leaf, fanout=args.fanout)
+    o = gb.opts(cutoff_b=args.cutoff, panel_nb=args.panel, leaf_rows=args.leaf, fanout=args.fanout,
+                fp64_gemm=gb.GBQR_GEMM_DMMA if args.fp64_gemm == "dmma" else gb.GBQR_GEMM_DFMA)
     nb = args.panel or gb.default_panel_nb(w.m, w.n)
     trows = w.n if layout == gb.GBQR_T_FULL else min(nb, w.n)
 
@@ -450,7 +453,7 @@ def run_gbqr(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed,
                        "t_layout": args.layout, "panel_nb": nb if layout == gb.GBQR_T_PANEL else None,
-                       "cutoff_b": args.cutoff or 16, "parallelism": f"replicas x{world}",
+                       "cutoff_b": args.cutoff or 16, "fp64_gemm": args.fp64_gemm, "parallelism": f"replicas x{world}",
                        "l2": "inputs (%.0f MB) larger than L2, no flush" % (w.m * w.n * 8 / 1e6),
                        "step": "restore A from a device copy + gbqr_factor"},
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": w.m * w.n * 8,

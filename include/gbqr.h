@@ -84,6 +84,10 @@ typedef enum {
                                FP64 otherwise, FP64 again when refinement stalls */
 } gbqr_prec;
 
+/* FP64 GEMM engine (gbqr_opts.fp64_gemm). */
+#define GBQR_GEMM_DMMA 1
+#define GBQR_GEMM_DFMA 2
+
 /* Algorithm parameters.  Zero selects the library's tuned default. */
 typedef struct {
     int32_t cutoff_b;   /* QR-EG base-case threshold b: base case when n <= b
@@ -101,7 +105,11 @@ typedef struct {
                            the tensor cores.  Reflector generation, the TSQR
                            R-merges and the in-panel products stay FP64. */
     int32_t batch_streams; /* gbqr_factor_batched: streams to spread over (1..128) */
-    int32_t reserved[1];
+    int32_t fp64_gemm;  /* FP64 GEMM tiles of 64 x 64 outputs: 0 or GBQR_GEMM_DFMA
+                           = CUDA-core FMA (default, measured faster);
+                           GBQR_GEMM_DMMA = FP64 tensor cores (mma.sync
+                           m8n8k4).  Both are deterministic and differ by
+                           rounding only. */
 } gbqr_opts;
 
 /* Device-side record of one or more calls since the last gbqr_sync(). */

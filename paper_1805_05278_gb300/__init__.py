@@ -27,6 +27,7 @@ GBQR_ENONFINITE, GBQR_ERANKDEF, GBQR_EBUSY, GBQR_EUNSUPPORTED, GBQR_ENOCONV = 5,
 # T layouts (gbqr_t_layout) and precisions (gbqr_prec)
 GBQR_T_FULL, GBQR_T_PANEL = 0, 1
 GBQR_FP64, GBQR_MIXED_BF16, GBQR_MIXED_SPLITBF16, GBQR_FP32, GBQR_PREC_AUTO = 0, 1, 2, 3, 4
+GBQR_GEMM_DMMA, GBQR_GEMM_DFMA = 1, 2
 GBQR_REQ_QUEUED, GBQR_REQ_RUNNING, GBQR_REQ_DONE = 0, 1, 2
 
 _I64 = ctypes.c_int64
@@ -37,7 +38,7 @@ class gbqr_opts(ctypes.Structure):
     _fields_ = [("cutoff_b", ctypes.c_int32), ("panel_nb", ctypes.c_int32),
                 ("leaf_rows", ctypes.c_int32), ("fanout", ctypes.c_int32),
                 ("lookahead", ctypes.c_int32), ("update_prec", ctypes.c_int32), ("batch_streams", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("fp64_gemm", ctypes.c_int32)]
 
 
 class gbqr_info(ctypes.Structure):
@@ -146,12 +147,14 @@ def check(status: int, what: str) -> int:
 
 
 def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int = 0,
-         lookahead: int = 0, update_prec: int = GBQR_FP64, batch_streams: int = 0) -> gbqr_opts:
+         lookahead: int = 0, update_prec: int = GBQR_FP64, batch_streams: int = 0,
+         fp64_gemm: int = 0) -> gbqr_opts:
     o = gbqr_opts()
     o.cutoff_b, o.panel_nb, o.leaf_rows, o.fanout = cutoff_b, panel_nb, leaf_rows, fanout
     o.lookahead = lookahead
     o.update_prec = update_prec
     o.batch_streams = batch_streams
+    o.fp64_gemm = fp64_gemm
     return o
 
 

@@ -76,6 +76,7 @@ struct Params {
     int fanout = kDefaultFanout;
     bool lookahead = true;
     int nsplit = 0;        // 0: FP64 updates; 1..3: split-BF16 tensor-core updates
+    bool dmma = false;     // FP64 GEMM engine of 64 x 64 tiles: DFMA (0.94 vs 0.83 TFLOP/s on 8192^2)
 };
 
 bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
@@ -95,6 +96,8 @@ bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
         if (o->update_prec == GBQR_MIXED_BF16) r.nsplit = 1;
         else if (o->update_prec == GBQR_MIXED_SPLITBF16) r.nsplit = 3;
         else if (o->update_prec != GBQR_FP64) return false;
+        if (o->fp64_gemm == GBQR_GEMM_DMMA) r.dmma = true;
+        else if (o->fp64_gemm != 0 && o->fp64_gemm != GBQR_GEMM_DFMA) return false;
     }
     r.nb = std::max<int64_t>(1, r.nb);
     *p = r;
@@ -241,6 +244,7 @@ void carve_work(gbqr_ctx *cx, char *base, const Layout &L, const Params &pr, con
     w->pr = pr;
     w->L = L;
     w->ex = ex;
+    w->ex.dmma = pr.dmma;
     w->gs.partial = (double *)(base + w->L.partial);
     w->gs.partial_elems = w->L.n_partial;
     w->gs.counters = (unsigned *)(base + w->L.gcount);

@@ -29,6 +29,7 @@ struct Exec {
     int64_t *launches = nullptr;
     int num_sms = 152;
     int device = 0;
+    bool dmma = false;          // 64 x 64 FP64 GEMM tiles on the FP64 tensor cores (else DFMA)
 };
 
 inline void trace_begin(const Exec &ex, Family f) {

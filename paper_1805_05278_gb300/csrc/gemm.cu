@@ -185,6 +185,147 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
     }
 }
 
+// 64 x 64 tiles on the FP64 tensor cores: mma.sync m8n8k4 (DMMA).  Same
+// staging, masks, K-range trimming and split-K tree as dgemm_kernel; 8 warps
+// as 2 (M) x 4 (N), each owning a 32 x 16 block = 4 x 2 MMA tiles.  Fragment
+// layouts of m8n8k4.f64: A (8x4, row) lane -> (lane/4, lane%4); B (4x8, col)
+// lane -> (lane%4, lane/4); C/D (8x8) lane -> (lane/4, 2*(lane%4) + i).
+__device__ __forceinline__ void dmma_8x8x4(double &d0, double &d1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(d0), "+d"(d1)
+                 : "d"(a), "d"(b));
+}
+
+template <bool TA>
+__global__ void __launch_bounds__(kThreads) dgemm_dmma_kernel(GemmParams p) {
+    constexpr int BM = 64, BN = 64;
+    // Row stride 68 = 4 (mod 16) doubles: the fragment loads (4 k-rows x 8
+    // consecutive columns per warp) then touch 16 distinct bank pairs per half-warp.
+    __shared__ double As[BK][BM + 4];
+    __shared__ double Bs[BK][BN + 4];
+    __shared__ int s_last;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp & 1, wn = warp >> 1;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    const int S = gridDim.z, z = blockIdx.z;
+
+    int64_t kb, ke;
+    k_range(p, TA, m0, n0, BM, BN, kb, ke);
+    int64_t k_lo = kb, k_hi = kb;
+    if (ke > kb) {
+        int64_t chunk = (ke - kb + S - 1) / S;
+        chunk = (chunk + BK - 1) / BK * BK;
+        k_lo = kb + (int64_t)z * chunk;
+        k_hi = min(ke, k_lo + chunk);
+    }
+
+    double acc[4][2][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) { acc[a][b][0] = 0.0; acc[a][b][1] = 0.0; }
+
+    for (int64_t k0 = k_lo; k0 < k_hi; k0 += BK) {
+#pragma unroll
+        for (int idx = tid; idx < BM * BK; idx += kThreads) {
+            int i, kk;
+            if (!TA) { i = idx % BM; kk = idx / BM; }
+            else     { kk = idx % BK; i = idx / BK; }
+            const int64_t gi = m0 + i, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < p.M && gk < k_hi) v = TA ? masked(p.A, p.lda, gk, gi, p.maskA)
+                                              : masked(p.A, p.lda, gi, gk, p.maskA);
+            As[kk][i] = v;
+        }
+#pragma unroll
+        for (int idx = tid; idx < BK * BN; idx += kThreads) {
+            const int kk = idx % BK, j = idx / BK;
+            const int64_t gk = k0 + kk, gj = n0 + j;
+            double v = 0.0;
+            if (gj < p.N && gk < k_hi) v = masked(p.B, p.ldb, gk, gj, p.maskB);
+            Bs[kk][j] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kq = 0; kq < BK; kq += 4) {
+            double a[4], b[2];
+#pragma unroll
+            for (int ms = 0; ms < 4; ++ms) a[ms] = As[kq + (lane & 3)][wm * 32 + ms * 8 + (lane >> 2)];
+#pragma unroll
+            for (int ns = 0; ns < 2; ++ns) b[ns] = Bs[kq + (lane & 3)][wn * 16 + ns * 8 + (lane >> 2)];
+#pragma unroll
+            for (int ms = 0; ms < 4; ++ms)
+#pragma unroll
+                for (int ns = 0; ns < 2; ++ns) dmma_8x8x4(acc[ms][ns][0], acc[ms][ns][1], a[ms], b[ns]);
+        }
+        __syncthreads();
+    }
+
+    // element q = (ms, ns, i) of this thread sits at tile row/col:
+    auto row_of = [&](int ms) { return wm * 32 + ms * 8 + (lane >> 2); };
+    auto col_of = [&](int ns, int i) { return wn * 16 + ns * 8 + 2 * (lane & 3) + i; };
+
+    if (S > 1) {
+        const int64_t tile = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
+        double *tp = p.partial + (size_t)tile * p.slots_per_tile * (BM * BN);
+        unsigned *tc = p.counters + (size_t)tile * p.counters_per_tile;
+        int slot = z, Sl = S, base = 0, cbase = 0;
+        for (;;) {
+            double *dst = tp + (size_t)(base + slot) * (BM * BN);
+#pragma unroll
+            for (int ms = 0; ms < 4; ++ms)
+#pragma unroll
+                for (int ns = 0; ns < 2; ++ns)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) dst[row_of(ms) + col_of(ns, i) * BM] = acc[ms][ns][i];
+            const int group = slot / kGroup, first = group * kGroup;
+            const int cnt = min(kGroup, Sl - first);
+            const int Snext = (Sl + kGroup - 1) / kGroup;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) {
+                unsigned prev = atomicAdd(&tc[cbase + group], 1u);
+                s_last = (prev == (unsigned)(cnt - 1));
+            }
+            __syncthreads();
+            if (!s_last) return;
+            __threadfence();
+            if (tid == 0) tc[cbase + group] = 0u;
+#pragma unroll
+            for (int ms = 0; ms < 4; ++ms)
+#pragma unroll
+                for (int ns = 0; ns < 2; ++ns)
+#pragma unroll
+                    for (int i = 0; i < 2; ++i) {
+                        double s = 0.0;
+                        for (int q = 0; q < cnt; ++q)
+                            s += __ldcg(tp + (size_t)(base + first + q) * (BM * BN) + row_of(ms) + col_of(ns, i) * BM);
+                        acc[ms][ns][i] = s;
+                    }
+            if (Snext == 1) break;
+            base += Sl;
+            cbase += Snext;
+            slot = group;
+            Sl = Snext;
+        }
+    }
+
+#pragma unroll
+    for (int ms = 0; ms < 4; ++ms)
+#pragma unroll
+        for (int ns = 0; ns < 2; ++ns)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int64_t gi = m0 + row_of(ms), gj = n0 + col_of(ns, i);
+                if (gi >= p.M || gj >= p.N) continue;
+                double *cp = p.C + gi + gj * p.ldc;
+                double v = p.alpha * acc[ms][ns][i];
+                if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+                *cp = v;
+            }
+}
+
 int tile_for(int64_t d) { return d <= 16 ? 16 : (d <= 32 ? 32 : 64); }
 
 // Slots and counters per tile of the reduction tree for S splits.
@@ -286,10 +427,16 @@ gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc) {
     dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)S);
     trace_begin(ex, FAM_GEMM);
     cudaError_t e;
-    switch (BM) {
-        case 16: e = launch_bm<16>(BN, p, op.ta, grid, ex.stream); break;
-        case 32: e = launch_bm<32>(BN, p, op.ta, grid, ex.stream); break;
-        default: e = launch_bm<64>(BN, p, op.ta, grid, ex.stream); break;
+    if (BM == 64 && BN == 64 && ex.dmma) {
+        if (op.ta) dgemm_dmma_kernel<true><<<grid, kThreads, 0, ex.stream>>>(p);
+        else dgemm_dmma_kernel<false><<<grid, kThreads, 0, ex.stream>>>(p);
+        e = cudaPeekAtLastError();
+    } else {
+        switch (BM) {
+            case 16: e = launch_bm<16>(BN, p, op.ta, grid, ex.stream); break;
+            case 32: e = launch_bm<32>(BN, p, op.ta, grid, ex.stream); break;
+            default: e = launch_bm<64>(BN, p, op.ta, grid, ex.stream); break;
+        }
     }
     if (e != cudaSuccess) return GBQR_ECUDA;
     const double bytes = 8.0 * ((double)op.M * op.K + (double)op.K * op.N + (op.beta != 0.0 ? 2.0 : 1.0) * op.M * op.N);

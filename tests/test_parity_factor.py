@@ -181,3 +181,22 @@ def test_lookahead_on_and_off(gb, ctx, orc, m, n, nb, lookahead):
     o = gb.opts(panel_nb=nb, lookahead=lookahead)
     VR, T, nbr = _gpu.factor_gpu(ctx, a, gb.GBQR_T_PANEL, o)
     _gpu.compare_factor(a, VR, T, gb.GBQR_T_PANEL, nbr, orc, f"lookahead={lookahead} nb={nb}")
+
+
+@pytest.mark.parametrize("engine", ["dmma", "dfma"])
+@pytest.mark.parametrize("m,n,layout_name", [(3001, 700, "full"), (1500, 1500, "panel"), (20000, 260, "panel")])
+def test_fp64_gemm_engines(gb, ctx, orc, m, n, layout_name, engine):
+    """The FP64 update products run either on the FP64 tensor cores (mma.sync
+    m8n8k4) or on CUDA-core FMAs; both match the oracle, and the two differ
+    from each other by rounding only."""
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    a = workloads.graded(m, n, 40 + n, decades=3.0)
+    e = gb.GBQR_GEMM_DMMA if engine == "dmma" else gb.GBQR_GEMM_DFMA
+    VR, T, nbr = _gpu.factor_gpu(ctx, a, layout, gb.opts(fp64_gemm=e))
+    _gpu.compare_factor(a, VR, T, layout, nbr, orc, f"engine={engine}")
+
+
+def test_fp64_gemm_engine_rejects_unknown(gb, ctx):
+    a = workloads.gaussian(100, 40, 1)
+    with pytest.raises(gb.GbqrError):
+        _gpu.factor_gpu(ctx, a, gb.GBQR_T_FULL, gb.opts(fp64_gemm=7))
