@@ -60,6 +60,10 @@ def parse():
     p.add_argument("--cutoff", type=int, default=0)
     p.add_argument("--fp64-gemm", choices=["dmma", "dfma"], default="dfma",
                    help="engine of the 64 x 64 FP64 GEMM tiles")
+    p.add_argument("--autotune-ms", type=float, default=40000.0,
+                   help="wall-clock budget of gbqr_autotune before the timed region (0: library defaults)")
+    p.add_argument("--batched-autotune-ms", type=float, default=20000.0,
+                   help="budget of gbqr_autotune_batched for the batched measurement (0: defaults)")
     p.add_argument("--panel", type=int, default=0)
     p.add_argument("--leaf", type=int, default=0)
     p.add_argument("--fanout", type=int, default=0)
@@ -141,6 +145,11 @@ def measure_batched(gb, dev, args):
     ctx = gb.Context(dev, stream)
     flops = sum(workloads.qr_flops(m, n) for (m, n) in shapes)
     o = gb.opts(batch_streams=args.batched_streams, cutoff_b=args.batched_cutoff)
+    tuned, tune_ms = None, None
+    if args.batched_autotune_ms > 0 and not (args.batched_streams or args.batched_cutoff):
+        with torch.cuda.stream(stream):
+            o, tune_ms = ctx.autotune_batched(shapes, gb.GBQR_FP64, args.batched_autotune_ms)
+        tuned = gb.opts_dict(o)
     with torch.cuda.stream(stream):
         ctx.factor_batched(As, Ts, o)                   # warm-up: lanes, workspace
         torch.cuda.synchronize()
@@ -162,7 +171,8 @@ def measure_batched(gb, dev, args):
     return {"workload": f"{len(shapes)} FP64 matrices, m log-uniform [256, 16384], n uniform [16, 256], seed {workloads.BATCHED_SEED}",
             "total_flops": flops, "ms_per_batch": ms, "tflops": flops / (ms * 1e-3) / 1e12,
             "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st),
-            "streams": args.batched_streams or 128, "cutoff_b": args.batched_cutoff or 16}
+            "streams": o.batch_streams or 128, "cutoff_b": o.cutoff_b or 16,
+            "tuned": tuned, "tuned_ms": tune_ms}
 
 
 def measure_ls(gb, ctx, dev, args):
@@ -360,13 +370,19 @@ def run_gbqr(args):
     layout = gb.GBQR_T_PANEL if args.layout == "panel" else gb.GBQR_T_FULL
     o = gb.opts(cutoff_b=args.cutoff, panel_nb=args.panel, leaf_rows=args.leaf, fanout=args.fanout,
                 fp64_gemm=gb.GBQR_GEMM_DMMA if args.fp64_gemm == "dmma" else gb.GBQR_GEMM_DFMA)
-    nb = args.panel or gb.default_panel_nb(w.m, w.n)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gb.Context(dev, stream)
+    # the tuner picks (b, k, leaf, nb, look-ahead, GEMM engine) unless any is given
+    tuned, tune_ms = None, None
+    explicit = args.cutoff or args.panel or args.leaf or args.fanout or args.fp64_gemm != "dfma"
+    if args.autotune_ms > 0 and not explicit:
+        o, tune_ms = ctx.autotune(w.m, w.n, layout, gb.GBQR_FP64, args.autotune_ms)
+        tuned = gb.opts_dict(o)
+    nb = o.panel_nb or gb.default_panel_nb(w.m, w.n)
     trows = w.n if layout == gb.GBQR_T_FULL else min(nb, w.n)
 
     seed = replica_seed(w.seed, rank)
     a_host = workloads.graded(w.m, w.n, seed) if w.graded else workloads.gaussian(w.m, w.n, seed)
-    stream = torch.cuda.current_stream(dev)
-    ctx = gb.Context(dev, stream)
     A0 = gb.to_colmajor(a_host, f"cuda:{dev}")
     A = gb.colmajor(w.m, w.n, f"cuda:{dev}")
     T = gb.colmajor(trows, w.n, f"cuda:{dev}")
@@ -453,7 +469,9 @@ def run_gbqr(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed,
                        "t_layout": args.layout, "panel_nb": nb if layout == gb.GBQR_T_PANEL else None,
-                       "cutoff_b": args.cutoff or 16, "fp64_gemm": args.fp64_gemm, "parallelism": f"replicas x{world}",
+                       "cutoff_b": o.cutoff_b or 16, "fanout": o.fanout or 8, "leaf_rows": o.leaf_rows,
+                       "lookahead": o.lookahead, "fp64_gemm": "dmma" if o.fp64_gemm == gb.GBQR_GEMM_DMMA else "dfma",
+                       "autotuned": tuned is not None, "autotune_ms": tune_ms, "parallelism": f"replicas x{world}",
                        "l2": "inputs (%.0f MB) larger than L2, no flush" % (w.m * w.n * 8 / 1e6),
                        "step": "restore A from a device copy + gbqr_factor"},
             "e2e": {"value": e2e_value, "unit": "TFLOP/s", "h2d_bytes_per_step": w.m * w.n * 8,

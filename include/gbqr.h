@@ -281,6 +281,51 @@ GBQR_API gbqr_status gbqr_gemm_split_bf16(gbqr_ctx *ctx, int transa, int64_t M, 
                                           double alpha, const double *A, int64_t lda, const double *B,
                                           int64_t ldb, double beta, double *C, int64_t ldc, int nsplit);
 
+/* ---- autotuner ------------------------------------------------------------ */
+
+/* The paper chooses its block sizes (the cutoff b of Algorithm 2, the TSQR
+ * tree of Section 5 / Appendix C, the panel width of Section 8.4's
+ * right-looking top level) from a cost model of a distributed machine.  Here
+ * they are measured: coordinate descent from the library defaults over
+ * cutoff_b {8,16,32,64}, fanout {2,4,8}, leaf_rows {default,128,...,1024},
+ * and for PANEL panel_nb {64,...,256} and lookahead, and for FP64 the GEMM
+ * engine; each candidate is gbqr_factor on a synthetic m x n matrix, timed
+ * with CUDA events on the context's stream (best of 2-5 runs after a
+ * warm-up); a candidate must win by 1%.  Trials stop when the next would
+ * overrun budget_ms of wall clock (the first measurement always runs).
+ *
+ * The winner is written to *best (every field explicit), its time to
+ * *best_ms (may be NULL), and cached in the context for the power-of-two
+ * class of (m, n), t_layout and update_prec.  Later calls of gbqr_factor and
+ * gbqr_ls_solve on this context take the cached values for every option
+ * field the caller leaves zero — except panel_nb in gbqr_factor, which fixes
+ * the caller's T layout (pass best->panel_nb explicitly, with ldt >= it).
+ * Synchronous; allocates m*n + 256*n doubles for the duration.
+ * Errors: EINVAL (m < n, n < 1, bad layout/precision, FULL with mixed),
+ * ENOMEM, ECUDA. */
+#define GBQR_TUNE_FACTOR 0
+#define GBQR_TUNE_BATCHED 1
+GBQR_API gbqr_status gbqr_autotune(gbqr_ctx *ctx, int64_t m, int64_t n, int t_layout, int update_prec,
+                                   double budget_ms, gbqr_opts *best, double *best_ms);
+
+/* The same for gbqr_factor_batched on `count` matrices of shapes (m[i], n[i])
+ * (synthetic contents, one buffer): batch_streams {16,...,128}, cutoff_b
+ * {8,16,32}, fanout {2,4,8}, leaf_rows {default,256,512}.  Each candidate
+ * is captured into a CUDA graph on a private stream and its graph launches
+ * are timed (the way a batch is meant to run; eager enqueueing of thousands
+ * of launches is host-bound).  EBUSY while tracing is on.  Cached per
+ * update_prec; gbqr_factor_batched then uses it for zero fields.  The cached
+ * batch_streams changes the workspace gbqr_factor_batched needs: query
+ * gbqr_batched_workspace_bytes with *best.  Allocates sum(m_i n_i + n_i^2)
+ * doubles for the duration.  Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_autotune_batched(gbqr_ctx *ctx, int count, const int64_t *m, const int64_t *n,
+                                           int update_prec, double budget_ms, gbqr_opts *best, double *best_ms);
+
+/* The cached result for kind GBQR_TUNE_FACTOR (shape class of m, n; layout;
+ * precision) or GBQR_TUNE_BATCHED (precision only).  EINVAL when none. */
+GBQR_API gbqr_status gbqr_tuned_lookup(const gbqr_ctx *ctx, int kind, int64_t m, int64_t n, int t_layout,
+                                       int update_prec, gbqr_opts *out);
+
 /* ---- serving: least squares with continuous batching -------------------- */
 
 typedef enum { GBQR_REQ_QUEUED = 0, GBQR_REQ_RUNNING = 1, GBQR_REQ_DONE = 2 } gbqr_req_state;

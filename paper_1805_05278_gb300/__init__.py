@@ -28,6 +28,7 @@ GBQR_ENONFINITE, GBQR_ERANKDEF, GBQR_EBUSY, GBQR_EUNSUPPORTED, GBQR_ENOCONV = 5,
 GBQR_T_FULL, GBQR_T_PANEL = 0, 1
 GBQR_FP64, GBQR_MIXED_BF16, GBQR_MIXED_SPLITBF16, GBQR_FP32, GBQR_PREC_AUTO = 0, 1, 2, 3, 4
 GBQR_GEMM_DMMA, GBQR_GEMM_DFMA = 1, 2
+GBQR_TUNE_FACTOR, GBQR_TUNE_BATCHED = 0, 1
 GBQR_REQ_QUEUED, GBQR_REQ_RUNNING, GBQR_REQ_DONE = 0, 1, 2
 
 _I64 = ctypes.c_int64
@@ -98,6 +99,12 @@ SIGNATURES = {
     "gbqr_trace_read": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_trace_rec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_launch_count": (_I64, [_P]),
     "gbqr_tsqr_static": (ctypes.c_int, [_I64, _I64, _P, _I64, _P, _I64, _P]),
+    "gbqr_autotune": (ctypes.c_int, [_P, _I64, _I64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.POINTER(gbqr_opts), ctypes.POINTER(ctypes.c_double)]),
+    "gbqr_autotune_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.c_int,
+                                             ctypes.c_double, ctypes.POINTER(gbqr_opts), ctypes.POINTER(ctypes.c_double)]),
+    "gbqr_tuned_lookup": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(gbqr_opts)]),
     "gbqr_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gbqr_fp64_issue_cycles": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gbqr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -156,6 +163,11 @@ def opts(cutoff_b: int = 0, panel_nb: int = 0, leaf_rows: int = 0, fanout: int =
     o.batch_streams = batch_streams
     o.fp64_gemm = fp64_gemm
     return o
+
+
+def opts_dict(o: gbqr_opts) -> dict:
+    """The fields of a gbqr_opts as a plain dict."""
+    return {name: getattr(o, name) for name, _ in gbqr_opts._fields_}
 
 
 def _cm(x, name: str):
@@ -309,6 +321,31 @@ class Context:
             ms[i], ns[i], ldas[i], ldts[i], pa[i], pt[i] = m, n, lda, ldt, a_ptr, t_ptr
         return check(gbqr_factor_batched(self.handle, cnt, ms, ns, pa, ldas, pt, ldts,  # noqa: F821
                                          ctypes.byref(o) if o is not None else None), "gbqr_factor_batched")
+
+    # ---- autotuner
+    def autotune(self, m: int, n: int, layout: int = GBQR_T_PANEL, prec: int = GBQR_FP64,
+                 budget_ms: float = 20000.0):
+        """gbqr_autotune: returns (best gbqr_opts, its time in ms); the result
+        is cached in this context for the shape class."""
+        o, ms = gbqr_opts(), ctypes.c_double()
+        check(gbqr_autotune(self.handle, m, n, layout, prec, budget_ms,  # noqa: F821
+                            ctypes.byref(o), ctypes.byref(ms)), "gbqr_autotune")
+        return o, ms.value
+
+    def autotune_batched(self, shapes, prec: int = GBQR_FP64, budget_ms: float = 20000.0):
+        """gbqr_autotune_batched over matrices of the given (m, n) shapes."""
+        cnt = len(shapes)
+        ms_, ns_ = (_I64 * cnt)(*[m for m, _ in shapes]), (_I64 * cnt)(*[n for _, n in shapes])
+        o, ms = gbqr_opts(), ctypes.c_double()
+        check(gbqr_autotune_batched(self.handle, cnt, ms_, ns_, prec, budget_ms,  # noqa: F821
+                                    ctypes.byref(o), ctypes.byref(ms)), "gbqr_autotune_batched")
+        return o, ms.value
+
+    def tuned(self, kind: int, m: int = 0, n: int = 0, layout: int = GBQR_T_PANEL, prec: int = GBQR_FP64):
+        """The cached tuner result, or None."""
+        o = gbqr_opts()
+        st = gbqr_tuned_lookup(self.handle, kind, m, n, layout, prec, ctypes.byref(o))  # noqa: F821
+        return o if st == GBQR_OK else None
 
     def capture(self, fn):
         """Run fn() under a capture of this context's stream; returns a Graph."""

@@ -13,7 +13,9 @@
 #include <climits>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 using namespace gbqr;
@@ -178,6 +180,8 @@ struct gbqr_ctx {
     cudaEvent_t ev_panel = nullptr, ev_ready = nullptr, ev_fork = nullptr;
     std::vector<cudaStream_t> lanes;      // batched factorization: one stream per lane
     std::vector<cudaEvent_t> lane_done;
+    mutable std::mutex tuned_mu;           // autotuner results (gbqr_autotune*)
+    std::unordered_map<uint64_t, gbqr_opts> tuned;
 
     Exec exec() {
         Exec e;
@@ -190,7 +194,70 @@ struct gbqr_ctx {
     }
 };
 
+namespace gbqr {
+
+static int ilog2_ceil(int64_t v) {
+    int r = 0;
+    while (((int64_t)1 << r) < v && r < 62) ++r;
+    return r;
+}
+
+uint64_t tune_key(int kind, int64_t m, int64_t n, int t_layout, int update_prec) {
+    return ((uint64_t)(kind & 0xff) << 40) | ((uint64_t)ilog2_ceil(std::max<int64_t>(m, 1)) << 32) |
+           ((uint64_t)ilog2_ceil(std::max<int64_t>(n, 1)) << 24) | ((uint64_t)(t_layout & 0xff) << 8) |
+           (uint64_t)(update_prec & 0xff);
+}
+cudaStream_t ctx_stream(const gbqr_ctx *cx) { return cx->stream; }
+int ctx_device(const gbqr_ctx *cx) { return cx->device; }
+bool ctx_tracing(const gbqr_ctx *cx) { return cx->tracing; }
+void ctx_store_tuned(gbqr_ctx *cx, uint64_t key, const gbqr_opts &o) {
+    std::lock_guard<std::mutex> lk(cx->tuned_mu);
+    cx->tuned[key] = o;
+}
+bool ctx_lookup_tuned(const gbqr_ctx *cx, uint64_t key, gbqr_opts *o) {
+    std::lock_guard<std::mutex> lk(cx->tuned_mu);
+    auto it = cx->tuned.find(key);
+    if (it == cx->tuned.end()) return false;
+    *o = it->second;
+    return true;
+}
+void ctx_copy_tuned(const gbqr_ctx *from, gbqr_ctx *to) {
+    std::unordered_map<uint64_t, gbqr_opts> copy;
+    {
+        std::lock_guard<std::mutex> lk(from->tuned_mu);
+        copy = from->tuned;
+    }
+    std::lock_guard<std::mutex> lk(to->tuned_mu);
+    to->tuned = std::move(copy);
+}
+
+}  // namespace gbqr
+
 namespace {
+
+// Tuned parameters for a call: the cached autotuner result for this shape
+// class, with every non-zero field of the caller's options taking precedence.
+// The panel width changes the PANEL T layout the caller allocated and later
+// passes to apply_q, so it is only taken where the call owns T (allow_nb).
+const gbqr_opts *with_tuned(const gbqr_ctx *cx, int kind, int64_t m, int64_t n, int t_layout,
+                            const gbqr_opts *o, gbqr_opts *eff, bool allow_nb) {
+    const int prec = o ? o->update_prec : GBQR_FP64;
+    gbqr_opts t;
+    if (!ctx_lookup_tuned(cx, tune_key(kind, m, n, t_layout, prec), &t)) return o;
+    if (o) {
+        if (o->cutoff_b) t.cutoff_b = o->cutoff_b;
+        if (o->panel_nb) t.panel_nb = o->panel_nb;
+        if (o->leaf_rows) t.leaf_rows = o->leaf_rows;
+        if (o->fanout) t.fanout = o->fanout;
+        if (o->lookahead) t.lookahead = o->lookahead;
+        if (o->batch_streams) t.batch_streams = o->batch_streams;
+        if (o->fp64_gemm) t.fp64_gemm = o->fp64_gemm;
+    }
+    if (!allow_nb) t.panel_nb = o ? o->panel_nb : 0;
+    t.update_prec = prec;
+    *eff = t;
+    return eff;
+}
 
 // Per-call view of the carved workspace.
 struct Work {
@@ -639,6 +706,16 @@ gbqr_status gbqr_sync(gbqr_ctx *cx, gbqr_info *info) {
 gbqr_status gbqr_factor(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_t lda,
                         double *T, int64_t ldt, int t_layout, const gbqr_opts *opts) {
     if (!cx) return GBQR_EINVAL;
+    gbqr_opts eff;
+    return gbqr::factor_untuned(cx, m, n, A, lda, T, ldt, t_layout,
+                                with_tuned(cx, GBQR_TUNE_FACTOR, m, n, t_layout, opts, &eff, false));
+}
+
+}  // extern "C"
+
+gbqr_status gbqr::factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_t lda,
+                                 double *T, int64_t ldt, int t_layout, const gbqr_opts *opts) {
+    if (!cx) return GBQR_EINVAL;
     Params pr;
     if (!resolve(opts, m, n, &pr)) return GBQR_EINVAL;
     TRY(check_layout_args(m, n, lda, ldt, t_layout, pr.nb));
@@ -661,6 +738,8 @@ gbqr_status gbqr_factor(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_t l
         return GBQR_ECUDA;
     return cudaStreamSynchronize(cx->stream) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
 }
+
+extern "C" {
 
 static gbqr_status apply_entry(gbqr_ctx *cx, bool trans, int64_t m, int64_t n, const double *VR, int64_t lda,
                                const double *T, int64_t ldt, int layout, int64_t nb, int64_t nrhs,
@@ -723,7 +802,8 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     gbqr_opts o;
     memset(&o, 0, sizeof o);
     o.update_prec = prec;
-    if (!resolve(&o, m, n, &pr)) return GBQR_EINVAL;
+    gbqr_opts eff;
+    if (!resolve(with_tuned(cx, GBQR_TUNE_FACTOR, m, n, GBQR_T_PANEL, &o, &eff, true), m, n, &pr)) return GBQR_EINVAL;
     Work w;
     TRY(begin_work(cx, m, n, GBQR_T_PANEL, pr, &w));
     const int64_t nb = std::min<int64_t>(pr.nb, n);
@@ -793,6 +873,17 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
 
 gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, double *const *A,
                                 const int64_t *lda, double *const *T, const int64_t *ldt, const gbqr_opts *opts) {
+    if (!cx) return GBQR_EINVAL;
+    gbqr_opts eff;
+    return gbqr::factor_batched_untuned(cx, count, m, n, A, lda, T, ldt,
+                                        with_tuned(cx, GBQR_TUNE_BATCHED, 0, 0, GBQR_T_PANEL, opts, &eff, false));
+}
+
+}  // extern "C"
+
+gbqr_status gbqr::factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, double *const *A,
+                                         const int64_t *lda, double *const *T, const int64_t *ldt, const gbqr_opts *opts,
+                                         bool prepare_only) {
     if (!cx || count < 0) return GBQR_EINVAL;
     if (count == 0) return GBQR_OK;
     if (!m || !n || !A || !lda || !T || !ldt) return GBQR_EINVAL;
@@ -827,6 +918,7 @@ gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const
         cx->lanes.push_back(st);
         cx->lane_done.push_back(ev);
     }
+    if (prepare_only) return GBQR_OK;
     // largest problems first, each to the least loaded lane
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
@@ -860,6 +952,8 @@ gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const
     }
     return GBQR_OK;
 }
+
+extern "C" {
 
 size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *n, const gbqr_opts *opts) {
     if (count <= 0 || !m || !n) return 0;

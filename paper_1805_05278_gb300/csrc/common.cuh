@@ -153,4 +153,25 @@ gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool
 // y = a x + b y
 gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y);
 
+// ------------------------------------------------------------ tuner cache
+// Context accessors for the tuner (the context's layout lives in api.cu).
+// Keys: kind (GBQR_TUNE_FACTOR / GBQR_TUNE_BATCHED), the power-of-two classes
+// of m and n, the T layout and the update precision.
+uint64_t tune_key(int kind, int64_t m, int64_t n, int t_layout, int update_prec);
+cudaStream_t ctx_stream(const gbqr_ctx *cx);
+int ctx_device(const gbqr_ctx *cx);
+bool ctx_tracing(const gbqr_ctx *cx);
+void ctx_store_tuned(gbqr_ctx *cx, uint64_t key, const gbqr_opts &o);
+bool ctx_lookup_tuned(const gbqr_ctx *cx, uint64_t key, gbqr_opts *o);
+void ctx_copy_tuned(const gbqr_ctx *from, gbqr_ctx *to);
+// gbqr_factor / gbqr_factor_batched without the tuner cache (the tuner's own
+// measurements must see exactly the options it passes)
+gbqr_status factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt,
+                           int t_layout, const gbqr_opts *opts);
+// prepare_only: validate, create the lane streams and size the workspace,
+// enqueue nothing (what a graph capture of the same call needs beforehand).
+gbqr_status factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, double *const *A,
+                                   const int64_t *lda, double *const *T, const int64_t *ldt, const gbqr_opts *opts,
+                                   bool prepare_only = false);
+
 }  // namespace gbqr

@@ -16,6 +16,7 @@
 // what FP32-level updates can refine).
 #include "common.cuh"
 
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <condition_variable>
@@ -47,10 +48,16 @@ int auto_precision(int64_t m, int64_t n) {
     return (n > 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
 }
 
-size_t footprint_of(const gbqr_request &r, int prec) {
+// Workspace of gbqr_ls_solve for this request: its shape and precision, with
+// the serving context's autotuned parameters where it has some (the workers
+// carry a copy of that cache, so they size their work the same way).
+size_t footprint_of(const gbqr_ctx *cx, const gbqr_request &r, int prec) {
     gbqr_opts o;
     memset(&o, 0, sizeof o);
-    o.update_prec = (prec == GBQR_FP64) ? GBQR_FP64 : prec;
+    if (gbqr::ctx_lookup_tuned(cx, gbqr::tune_key(GBQR_TUNE_FACTOR, r.m, r.n, GBQR_T_PANEL, prec), &o)) {
+        o.batch_streams = 0;
+    }
+    o.update_prec = prec;
     return gbqr_workspace_bytes(r.m, r.n, GBQR_T_PANEL, &o) + ((size_t)1 << 20);
 }
 
@@ -183,6 +190,7 @@ GBQR_API gbqr_status gbqr_server_start(gbqr_ctx *ctx, int device, int workers, s
         gbqr_ctx *wc = nullptr;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) break;
         if (gbqr_create(&wc, device, st) != GBQR_OK) { cudaStreamDestroy(st); break; }
+        gbqr::ctx_copy_tuned(ctx, wc);
         sv->streams.push_back(st);
         sv->ctxs.push_back(wc);
     }
@@ -207,7 +215,10 @@ GBQR_API gbqr_status gbqr_submit(gbqr_ctx *ctx, const gbqr_request *req, uint64_
         return GBQR_EINVAL;
     Record rec;
     rec.req = r;
-    rec.footprint = footprint_of(r, r.prec == GBQR_PREC_AUTO ? auto_precision(r.m, r.n) : r.prec);
+    // AUTO may fall back to FP64 inside the same workspace: size for both
+    rec.footprint = (r.prec == GBQR_PREC_AUTO)
+                        ? std::max(footprint_of(ctx, r, auto_precision(r.m, r.n)), footprint_of(ctx, r, GBQR_FP64))
+                        : footprint_of(ctx, r, r.prec);
     if (rec.footprint > sv->cap) return GBQR_ENOMEM;
     rec.t_submit = Clock::now();
     {

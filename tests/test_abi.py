@@ -79,6 +79,9 @@ def test_null_and_invalid_arguments_without_gpu(lib):
     assert gb.gbqr_destroy(None) == gb.GBQR_EINVAL
     assert gb.gbqr_factor(None, 4, 2, None, 4, None, 2, 0, None) == gb.GBQR_EINVAL
     assert gb.gbqr_sync(None, None) == gb.GBQR_EINVAL
+    assert gb.gbqr_autotune(None, 100, 10, 1, 0, 1.0, None, None) == gb.GBQR_EINVAL
+    assert gb.gbqr_autotune_batched(None, 1, None, None, 0, 1.0, None, None) == gb.GBQR_EINVAL
+    assert gb.gbqr_tuned_lookup(None, 0, 100, 10, 1, 0, None) == gb.GBQR_EINVAL
 
 
 def test_create_fails_loudly_without_a_gpu(lib):
