@@ -67,8 +67,9 @@ def parse():
     p.add_argument("--panel", type=int, default=0)
     p.add_argument("--leaf", type=int, default=0)
     p.add_argument("--fanout", type=int, default=0)
-    p.add_argument("--ls-solves", type=int, default=5, help="timed least-squares solves per precision (0: skip)")
-    p.add_argument("--ls-decades", type=float, default=4.0)
+    p.add_argument("--ls-solves", type=int, default=3, help="timed least-squares solves per grid point and precision (0: skip)")
+    p.add_argument("--ls-decades", default="2,6,10", help="column-grading decades (kappa ~ 10^d x kappa(Gaussian))")
+    p.add_argument("--ls-shapes", default="32768x2048,8192x8192")
     p.add_argument("--batched", type=int, default=2000, help="matrices in the batched measurement (0: skip)")
     p.add_argument("--batched-steps", type=int, default=3)
     p.add_argument("--batched-streams", type=int, default=0)
@@ -175,41 +176,88 @@ def measure_batched(gb, dev, args):
             "tuned": tuned, "tuned_ms": tune_ms}
 
 
-def measure_ls(gb, ctx, dev, args):
-    """Least-squares solves (32768 x 2048, graded columns, b = A x_true + 1e-8
-    noise): FP64 path vs mixed path (tensor-core split-BF16 updates + FP64
-    refinement).  Each solve timed alone with CUDA events; solves/s = count /
-    summed time; p50 / p99 over the solves."""
+def kappa_estimate(R, iters: int = 40) -> float:
+    """sigma_max / sigma_min of the n x n upper triangular R (= kappa_2(A)),
+    by power iteration on R^T R and inverse power iteration with two
+    triangular solves per step (measurement only: torch on the device)."""
     import torch
-    m, n = 32768, 2048
-    a, xt, b = workloads.ls_problem(m, n, args.ls_decades, 11)
-    A = gb.to_colmajor(a, f"cuda:{dev}")
-    bd = torch.from_numpy(b).to(f"cuda:{dev}")
-    xtd = torch.from_numpy(xt).to(f"cuda:{dev}")
-    out, xs = {}, {}
+    g = torch.Generator(device=R.device)
+    g.manual_seed(0)
+    v = torch.randn(R.shape[0], 1, dtype=torch.float64, device=R.device, generator=g)
+    u = v.clone()
+    smax2 = smin2_inv = 0.0
+    for _ in range(iters):
+        v = R.T @ (R @ v)
+        smax2 = float(torch.linalg.norm(v))
+        v /= smax2
+        y = torch.linalg.solve_triangular(R.T, u, upper=False)
+        u = torch.linalg.solve_triangular(R, y, upper=True)
+        smin2_inv = float(torch.linalg.norm(u))
+        u /= smin2_inv
+    return math.sqrt(smax2 * smin2_inv)
+
+
+def measure_ls(gb, ctx, dev, args):
+    """Least squares on the graded workloads (32768 x 2048 and 8192 x 8192,
+    column j scaled by 10^(-d j / n) for d in args.ls_decades, x_true iid
+    N(0,1), b = A x_true + 1e-8 N(0,1)), FP64 path vs mixed path (tensor-core
+    split-BF16 updates + FP64 refinement).  Each solve is timed alone with
+    CUDA events; solves/s = count / summed time; p50 / p99 over the solves.
+    Accuracy per result: error vs x_true, the mixed result vs the FP64
+    result, and the normwise backward error
+    ||A^T r|| / (||A||_F ||r|| + ||A||_F^2 ||x||) with r = b - A x, all in FP64.
+    kappa_2(A) is estimated from the FP64 R factor."""
+    import torch
+    devs = f"cuda:{dev}"
     stream = torch.cuda.current_stream(dev)
     ctx = gb.Context(dev, stream)        # its own, library-grown workspace
-    for prec, name in [(gb.GBQR_FP64, "fp64"), (gb.GBQR_MIXED_SPLITBF16, "mixed_splitbf16")]:
-        x = torch.zeros(n, dtype=torch.float64, device=f"cuda:{dev}")
-        st, info = ctx.ls_solve(A, bd, x, prec)          # warm-up
-        times = []
-        for _ in range(args.ls_solves):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st, info = ctx.ls_solve(A, bd, x, prec)
-            e1.record(stream)
+    shapes = [tuple(int(v) for v in s.split("x")) for s in args.ls_shapes.split(",") if s]
+    decades = [float(d) for d in str(args.ls_decades).split(",") if d]
+    grid = []
+    for (m, n) in shapes:
+        for d in decades:
+            seed = 11 + int(d)
+            A, xt, b = workloads.serving_device_problem(m, n, d, seed, devs)
+            af = float(torch.linalg.matrix_norm(A))
+            Af = A.clone()
+            Tf = gb.colmajor(min(gb.default_panel_nb(m, n), n), n, devs)
+            ctx.factor(Af, Tf, gb.GBQR_T_PANEL)
             torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
-        times.sort()
-        xs[name] = x.clone()
-        out[name] = {"status": int(st), "solves_per_s": len(times) / (sum(times) * 1e-3),
-                     "p50_ms": times[len(times) // 2], "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
-                     "refine_iters": int(info.refine_iters),
-                     "rel_err_vs_xtrue": float(torch.linalg.norm(x - xtd) / torch.linalg.norm(xtd))}
-    out["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(xs["mixed_splitbf16"] - xs["fp64"]) / torch.linalg.norm(xs["fp64"]))
-    out["workload"] = f"ls graded {m}x{n}, decades {args.ls_decades}, b = A x_true + 1e-8 N(0,1), seed 11"
+            kappa = kappa_estimate(torch.triu(Af[:n, :n]))
+            del Af, Tf
+            row = {"m": m, "n": n, "decades": d, "kappa_est": kappa, "seed": seed}
+            xs = {}
+            for prec, name in [(gb.GBQR_FP64, "fp64"), (gb.GBQR_MIXED_SPLITBF16, "mixed_splitbf16")]:
+                x = torch.zeros(n, dtype=torch.float64, device=devs)
+                st, info = ctx.ls_solve(A, b, x, prec)          # warm-up
+                times = []
+                for _ in range(args.ls_solves):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st, info = ctx.ls_solve(A, b, x, prec)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                times.sort()
+                xs[name] = x.clone()
+                r = b - A @ x
+                bwd = float(torch.linalg.norm(A.T @ r)) / (af * float(torch.linalg.norm(r)) + af * af * float(torch.linalg.norm(x)))
+                row[name] = {"status": int(st), "solves_per_s": len(times) / (sum(times) * 1e-3),
+                             "p50_ms": times[len(times) // 2],
+                             "p99_ms": times[min(len(times) - 1, int(0.99 * len(times)))],
+                             "refine_iters": int(info.refine_iters), "refine_last": float(info.refine_last),
+                             "gmres_steps": int(info.gmres_steps), "lib_backward_err": float(info.backward_err),
+                             "rel_err_vs_xtrue": float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)),
+                             "backward_err": bwd}
+            row["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(xs["mixed_splitbf16"] - xs["fp64"]) /
+                                                  torch.linalg.norm(xs["fp64"]))
+            row["speedup_mixed"] = row["mixed_splitbf16"]["solves_per_s"] / row["fp64"]["solves_per_s"]
+            grid.append(row)
+            del A, b, xt
+            torch.cuda.empty_cache()
     ctx.close()
-    return out
+    return {"workload": "ls graded m x n, column j scaled 10^(-d j/n), x_true N(0,1), b = A x_true + 1e-8 N(0,1), "
+                        "seeded torch generator (seed 11 + d)", "solves_per_point": args.ls_solves, "grid": grid}
 
 
 # ------------------------------------------------------------- multi-rank

@@ -119,7 +119,9 @@ typedef struct {
     int64_t rankdef_col;   /* least squares: first j with R(j,j) == 0, else -1 */
     int64_t refine_iters;  /* least squares, mixed precision: refinement steps taken */
     double refine_last;    /* ... and ||dx|| / ||x|| of the last step */
-    int64_t reserved[3];
+    int64_t gmres_steps;   /* least squares, mixed: Arnoldi steps of GMRES refinement */
+    double backward_err;   /* least squares: ||A^T s|| / (||A||_F ||s|| + ||A||_F^2 ||x||), s = b - A x */
+    int64_t reserved[1];
 } gbqr_info;
 
 /* Per-kernel-family totals of traced launches (see gbqr_trace_enable). */
@@ -251,14 +253,24 @@ GBQR_API gbqr_status gbqr_form_q(gbqr_ctx *ctx, int64_t m, int64_t n, const doub
  *     products of the factorization run on the tensor cores (3 or 1 BF16
  *     slices, FP32 accumulation; reflectors and R-merges stay FP64), then
  *     the solution is refined on the augmented system [I A; A^T 0][r; x] =
- *     [b; 0] with FP64 residuals until ||dx|| / ||x|| stops decreasing or
- *     falls below 1e-16 (at most 40 steps).  Converges when kappa(A) times
- *     the factorization's precision is well below 1.
+ *     [b; 0] with FP64 residuals: each correction is GMRES on Bjorck's
+ *     scaled system [aI A; A^T 0] (a ~ sigma_min / sqrt 2) preconditioned by
+ *     the mixed factors (up to 8 corrections of at most 100 Arnoldi steps;
+ *     GMRES-IR of Carson, Higham and Pranesh).  Unlike classical refinement
+ *     it does not need kappa(A) u_f < 1 (u_f ~ 2^-22 for three slices).
+ * Success means the normwise backward error
+ *   eta = ||A^T s|| / (||A||_F ||s|| + ||A||_F^2 ||x||),  s = b - A x,
+ * computed in FP64, is at most 4 u (1 + sqrt(m) ||s|| / (||s|| + ||A||_F ||x||))
+ * (u = 2^-53: the level that rounding in forming s and A^T s leaves even for
+ * the exact solution); the FP64 path always reports success (eta is
+ * reported only).
  * b has m entries, x receives n (device pointers).  info (may be NULL)
- * receives rankdef_col and, for the mixed path, refine_iters / refine_last.
+ * receives rankdef_col, backward_err and, for the mixed path, refine_iters
+ * (corrections applied), refine_last, gmres_steps.
  * Synchronous: returns after x is written.
  * Errors: EINVAL, ENOMEM, ECUDA, ERANKDEF (an exactly zero R(j,j)),
- * ENOCONV (mixed refinement stalled above 1e-12), EUNSUPPORTED. */
+ * ENOCONV (mixed: backward error above target after refinement),
+ * EUNSUPPORTED. */
 GBQR_API gbqr_status gbqr_ls_solve(gbqr_ctx *ctx, int64_t m, int64_t n, const double *A, int64_t lda,
                           const double *b, double *x, int prec, gbqr_info *info);
 

@@ -45,7 +45,8 @@ class gbqr_opts(ctypes.Structure):
 class gbqr_info(ctypes.Structure):
     _fields_ = [("nonfinite", ctypes.c_int64), ("zero_pivots", ctypes.c_int64),
                 ("rankdef_col", ctypes.c_int64), ("refine_iters", ctypes.c_int64),
-                ("refine_last", ctypes.c_double), ("reserved", ctypes.c_int64 * 3)]
+                ("refine_last", ctypes.c_double), ("gmres_steps", ctypes.c_int64),
+                ("backward_err", ctypes.c_double), ("reserved", ctypes.c_int64 * 1)]
 
 
 class gbqr_request(ctypes.Structure):

@@ -27,6 +27,7 @@ constexpr int kDefaultFanout = 0;   // 0: the TSQR planner chooses
 constexpr int64_t kDefaultPanel = 128;
 constexpr int kBatchLanes = 128;      // streams a batched factorization spreads over (measured best of 16..128)
 constexpr int kBatchCutoff = 16;      // batched default cutoff b (measured best of 16, 32)
+constexpr int kKrylov = 100;          // GMRES refinement: Arnoldi steps per correction
 constexpr int kMaxBatchLanes = 128;
 
 struct DeviceInfo {
@@ -112,6 +113,7 @@ struct Layout {
     size_t M1 = 0, M2 = 0, bigA = 0, bigT = 0, vec = 0;
     size_t partial2 = 0, gcount2 = 0, M1b = 0, M2b = 0;   // second lane (look-ahead panel stream)
     size_t tc = 0, n_tc = 0;                              // tensor-core slices (mixed updates)
+    size_t kry = 0, n_kry = 0;                            // least squares, mixed: Krylov basis of the refinement
     size_t total = 0;
     size_t n_partial = 0, n_gcount = 0, n_M = 0, n_Mb = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
     TsqrPlan tsqr;
@@ -159,6 +161,12 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     L.bigT = take(L.n_bigT * 8);
     // least squares: vectors f, r (m) and x, dx, g (n) of the refinement
     L.vec = take(staging ? ((size_t)3 * std::max<int64_t>(m, 1) + 4 * (size_t)std::max<int64_t>(n, 1) + 16) * 8 : 16);
+    // GMRES refinement (mixed least squares): kKrylov + 2 vectors of m + n,
+    // and the projections and norms read back each Arnoldi step
+    if (staging && pr.nsplit > 0) {
+        L.n_kry = (size_t)(kKrylov + 2) * (size_t)(std::max<int64_t>(m, 1) + std::max<int64_t>(n, 1)) + 4 * (kKrylov + 2) + 16;
+        L.kry = take(L.n_kry * 8);
+    }
     L.total = off;
     return L;
 }
@@ -267,7 +275,7 @@ struct Work {
     Params pr;
     GemmScratch gs;
     TsqrWork tw;
-    double *M1, *M2, *bigA, *bigT, *vec;
+    double *M1, *M2, *bigA, *bigT, *vec, *kry;
     size_t n_M;                      // capacity of M1 / M2 of this lane
     TcScratch tcs;                   // tensor-core scratch (main lane, mixed updates)
     GemmScratch gs2;
@@ -326,6 +334,7 @@ void carve_work(gbqr_ctx *cx, char *base, const Layout &L, const Params &pr, con
     w->bigA = (double *)(base + w->L.bigA);
     w->bigT = (double *)(base + w->L.bigT);
     w->vec = (double *)(base + w->L.vec);
+    w->kry = w->L.n_kry ? (double *)(base + w->L.kry) : nullptr;
     w->n_M = w->L.n_M;
     w->gs2.partial = (double *)(base + w->L.partial2);
     w->gs2.partial_elems = pr.lookahead ? w->L.n_partial : 0;
@@ -820,43 +829,178 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
     TRY(copy_matrix(w.ex, n, 1, f, n, x, n));
     TRY(trsv_upper(w.ex, n, w.bigA, m, x, &di->rankdef));
+    // Refinement on the augmented system K [r; x] = [b; 0], K = [I A; A^T 0],
+    // with FP64 residuals.  The mixed QR solves K approximately (M^{-1}):
+    //   h = R^{-T} g,  d = Q^T f,  dx = R^{-1} (d(0:n) - h),  dr = Q [h; d(n:m)].
+    // Corrections are computed by GMRES on M^{-1} K with the mixed factors as
+    // preconditioner until the backward error reaches its target (the
+    // three-precision GMRES-IR for least squares of Carson, Higham and
+    // Pranesh, here with FP64 residuals and working precision and
+    // split-BF16 factors).
+    double *dr = g + n, *tmp = dr + m;                     // m and n doubles
+    auto read = [&](const double *dev, double *host, int count) -> gbqr_status {
+        if (cudaMemcpyAsync(host, dev, sizeof(double) * count, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess ||
+            cudaStreamSynchronize(cx->stream) != cudaSuccess)
+            return GBQR_ECUDA;
+        return GBQR_OK;
+    };
+    // normwise backward error of the LS solution, s = b - A x (FP64):
+    //   eta = ||A^T s|| / (||A||_F ||s|| + ||A||_F^2 ||x||),
+    // and the target it is held to: the level that rounding in forming s and
+    // A^T s in FP64 leaves even for the exact solution, about
+    //   u (1 + sqrt(m) ||s|| / (||s|| + ||A||_F ||x||))   (u = 2^-53),
+    // times 4.  Small-residual problems must reach a few u; large-residual
+    // ones are allowed the sqrt(m) u floor of the A^T s product.
+    TRY(frob2(w.ex, m, n, A, lda, tmp, nrm + 4));
+    double eta_tol = 0.0;
+    auto backward_error = [&](double *eta) -> gbqr_status {
+        TRY(copy_matrix(w.ex, m, 1, b, m, dr, m));
+        TRY(gemv_n(w.ex, m, n, A, lda, x, -1.0, 1.0, dr, w.gs.partial, w.gs.partial_elems));
+        TRY(gemv_t(w.ex, m, n, A, lda, dr, 1.0, 0.0, tmp));
+        TRY(norms2(w.ex, n, tmp, x, nrm));
+        TRY(norms2(w.ex, m, dr, dr, nrm + 2));
+        double h[5];
+        TRY(read(nrm, h, 5));
+        const double an = std::sqrt(h[4]), sn = std::sqrt(h[2]), axn = an * std::sqrt(h[1]);
+        const double den = an * sn + an * axn;
+        *eta = den > 0.0 ? std::sqrt(h[0]) / den : (h[0] > 0.0 ? INFINITY : 0.0);
+        const double wres = (sn + axn) > 0.0 ? sn / (sn + axn) : 1.0;
+        eta_tol = 4.0 * 0x1.0p-53 * (1.0 + std::sqrt((double)m) * wres);
+        return GBQR_OK;
+    };
     int iters = 0;
-    double last = 0.0;
-    bool converged = (prec == GBQR_FP64);
-    if (!converged) {
-        // Refinement on the augmented system [I A; A^T 0][r; x] = [b; 0] with
-        // FP64 residuals; each correction solved with the mixed QR:
-        //   f = b - r - A x,  g = -A^T r,  h = R^{-T} g,  d = Q^T f,
-        //   dx = R^{-1}(d(0:n) - h),  dr = Q [h; d(n:m)]
-        TRY(copy_matrix(w.ex, m, 1, b, m, r, m));
-        TRY(gemv_n(w.ex, m, n, A, lda, x, -1.0, 1.0, r, w.gs.partial, w.gs.partial_elems));
-        double prev = 1e300;
-        for (iters = 1; iters <= 40; ++iters) {
+    int64_t gmres_steps = 0;
+    double last = 0.0, eta = 0.0;
+    if (prec != GBQR_FP64) {
+        auto precond = [&](double *fv, double *gv, double *dxv) -> gbqr_status {
+            // in (fv, gv); out: dr in fv, dx in dxv; gv is overwritten (h)
+            TRY(trsv_upper_t(w.ex, n, w.bigA, m, gv, &di->rankdef));
+            TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, fv, m, false));
+            TRY(copy_matrix(w.ex, n, 1, fv, n, dxv, n));
+            TRY(axpby(w.ex, n, -1.0, gv, 1.0, dxv));
+            TRY(trsv_upper(w.ex, n, w.bigA, m, dxv, &di->rankdef));
+            TRY(copy_matrix(w.ex, n, 1, gv, n, fv, n));
+            return apply_q_any(w, false, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, fv, m, false);
+        };
+        auto residual = [&]() -> gbqr_status {          // f = b - r - A x, g = -A^T r
             TRY(copy_matrix(w.ex, m, 1, b, m, f, m));
             TRY(axpby(w.ex, m, -1.0, r, 1.0, f));
             TRY(gemv_n(w.ex, m, n, A, lda, x, -1.0, 1.0, f, w.gs.partial, w.gs.partial_elems));
-            TRY(gemv_t(w.ex, m, n, A, lda, r, -1.0, 0.0, g));
-            TRY(trsv_upper_t(w.ex, n, w.bigA, m, g, &di->rankdef));                 // g <- h
-            TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
-            TRY(copy_matrix(w.ex, n, 1, f, n, dx, n));
-            TRY(axpby(w.ex, n, -1.0, g, 1.0, dx));
-            TRY(trsv_upper(w.ex, n, w.bigA, m, dx, &di->rankdef));
-            TRY(copy_matrix(w.ex, n, 1, g, n, f, n));                               // f <- [h; d2]
-            TRY(apply_q_any(w, false, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
-            TRY(axpby(w.ex, n, 1.0, dx, 1.0, x));
-            TRY(axpby(w.ex, m, 1.0, f, 1.0, r));
-            TRY(norms2(w.ex, n, dx, x, nrm));
-            double hn[2] = {0.0, 0.0};
-            if (cudaMemcpyAsync(hn, nrm, sizeof hn, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess ||
+            return gemv_t(w.ex, m, n, A, lda, r, -1.0, 0.0, g);
+        };
+        auto step_ratio = [&](const double *dxv, double *ratio) -> gbqr_status {   // ||dx|| / ||x||
+            TRY(norms2(w.ex, n, dxv, x, nrm));
+            double hn[2];
+            TRY(read(nrm, hn, 2));
+            *ratio = hn[1] > 0.0 ? std::sqrt(hn[0] / hn[1]) : (hn[0] > 0.0 ? INFINITY : 0.0);
+            return GBQR_OK;
+        };
+        TRY(copy_matrix(w.ex, m, 1, b, m, r, m));
+        TRY(gemv_n(w.ex, m, n, A, lda, x, -1.0, 1.0, r, w.gs.partial, w.gs.partial_elems));
+        TRY(backward_error(&eta));
+        // GMRES-IR: each correction solves the augmented system by GMRES
+        // preconditioned with the mixed factors.  The Krylov space of M^{-1} K
+        // holds the iterates of classical refinement, so GMRES never needs
+        // more operator applications than it, and it keeps converging where
+        // kappa(A) u_f > 1 makes classical refinement diverge.  GMRES works on
+        // Bjorck's scaled system K_a [r / a; x] = [b; 0], K_a = [aI A; A^T 0]
+        // with a = sigma_min(A) / sqrt(2) (estimated by min |R(j,j)|): kappa(K_1)
+        // grows like kappa(A)^2, kappa(K_a) only like 2 kappa(A).  With
+        // D = diag(a I_m, I_n), K_a = D K_1 D in the variables D^{-1}[r; x],
+        // so the preconditioned operator is D^{-1} (M^{-1} K_1) D and the
+        // unscaled solves are reused.
+        if (eta > eta_tol && w.kry) {
+            const int64_t N = m + n;
+            std::vector<double> diag(n);
+            if (cudaMemcpy2DAsync(diag.data(), sizeof(double), w.bigA, (size_t)(m + 1) * sizeof(double),
+                                  sizeof(double), n, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess ||
                 cudaStreamSynchronize(cx->stream) != cudaSuccess)
                 return GBQR_ECUDA;
-            last = (hn[1] > 0.0) ? std::sqrt(hn[0] / hn[1]) : 0.0;
-            if (!(last == last)) break;                                   // NaN: stop
-            if (last <= 1e-16) { converged = true; break; }
-            if (iters >= 2 && last > 0.5 * prev) { converged = last <= 1e-12; break; }
-            prev = last;
+            double rmin = INFINITY;
+            for (double v : diag) rmin = std::min(rmin, std::fabs(v));
+            const double alpha = (rmin > 0.0 && std::isfinite(rmin)) ? rmin / std::sqrt(2.0) : 1.0;
+            double *V = w.kry;                                  // Arnoldi basis, kKrylov + 1 columns of N
+            double *dvec = V + (size_t)(kKrylov + 1) * N;       // the correction [dr; dx]
+            double *hd = dvec + N;                              // projections (2 x (kKrylov + 1)) and a norm
+            const int hstride = kKrylov + 1;
+            std::vector<double> H((size_t)(kKrylov + 1) * kKrylov, 0.0), cs(kKrylov), sn(kKrylov),
+                e(kKrylov + 1), hb(2 * hstride + 2), y(kKrylov);
+            for (int outer = 0; outer < 8 && eta > eta_tol; ++outer) {
+                TRY(residual());
+                TRY(copy_matrix(w.ex, m, 1, f, m, V, m));
+                TRY(copy_matrix(w.ex, n, 1, g, n, tmp, n));
+                TRY(precond(V, tmp, V + m));                    // v0 = D^{-1} M^{-1} [f; g]
+                TRY(axpby(w.ex, m, 1.0 / alpha, V, 0.0, V));
+                TRY(norms2(w.ex, N, V, V, nrm));
+                double h0[1];
+                TRY(read(nrm, h0, 1));
+                const double beta = std::sqrt(h0[0]);
+                if (!(beta > 0.0) || !std::isfinite(beta)) break;
+                TRY(axpby(w.ex, N, 1.0 / beta, V, 0.0, V));
+                std::fill(e.begin(), e.end(), 0.0);
+                e[0] = beta;
+                int k = 0;
+                for (int j = 0; j < kKrylov; ++j) {
+                    double *vj = V + (size_t)j * N, *wv = V + (size_t)(j + 1) * N;
+                    // w = D^{-1} M^{-1} K D v_j with K [t; u] = [t + A u; A^T t], t = a v_r
+                    TRY(axpby(w.ex, m, alpha, vj, 0.0, wv));
+                    TRY(gemv_t(w.ex, m, n, A, lda, wv, 1.0, 0.0, tmp));
+                    TRY(gemv_n(w.ex, m, n, A, lda, vj + m, 1.0, 1.0, wv, w.gs.partial, w.gs.partial_elems));
+                    TRY(precond(wv, tmp, wv + m));
+                    TRY(axpby(w.ex, m, 1.0 / alpha, wv, 0.0, wv));
+                    // classical Gram-Schmidt, twice
+                    TRY(gemv_t(w.ex, N, j + 1, V, N, wv, 1.0, 0.0, hd));
+                    TRY(gemv_n(w.ex, N, j + 1, V, N, hd, -1.0, 1.0, wv, w.gs.partial, w.gs.partial_elems));
+                    TRY(gemv_t(w.ex, N, j + 1, V, N, wv, 1.0, 0.0, hd + hstride));
+                    TRY(gemv_n(w.ex, N, j + 1, V, N, hd + hstride, -1.0, 1.0, wv, w.gs.partial, w.gs.partial_elems));
+                    TRY(norms2(w.ex, N, wv, wv, hd + 2 * hstride));
+                    TRY(read(hd, hb.data(), 2 * hstride + 1));
+                    double *Hj = H.data() + (size_t)j * (kKrylov + 1);
+                    for (int i = 0; i <= j; ++i) Hj[i] = hb[i] + hb[hstride + i];
+                    const double hnext = std::sqrt(hb[2 * hstride]);
+                    Hj[j + 1] = hnext;
+                    for (int i = 0; i < j; ++i) {                  // previous Givens rotations
+                        const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+                        Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+                        Hj[i] = t;
+                    }
+                    const double rho = std::hypot(Hj[j], Hj[j + 1]);
+                    cs[j] = rho > 0.0 ? Hj[j] / rho : 1.0;
+                    sn[j] = rho > 0.0 ? Hj[j + 1] / rho : 0.0;
+                    Hj[j] = rho;
+                    Hj[j + 1] = 0.0;
+                    e[j + 1] = -sn[j] * e[j];
+                    e[j] = cs[j] * e[j];
+                    k = j + 1;
+                    if (!(hnext > 0.0) || std::fabs(e[j + 1]) <= 1e-10 * beta) break;
+                    TRY(axpby(w.ex, N, 1.0 / hnext, wv, 0.0, wv));
+                }
+                // y = H(0:k, 0:k)^{-1} e(0:k); correction = V(:, 0:k) y
+                for (int i = k - 1; i >= 0; --i) {
+                    double t = e[i];
+                    for (int l = i + 1; l < k; ++l) t -= H[(size_t)l * (kKrylov + 1) + i] * y[l];
+                    const double d = H[(size_t)i * (kKrylov + 1) + i];
+                    y[i] = d != 0.0 ? t / d : 0.0;
+                }
+                if (cudaMemcpyAsync(hd, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, cx->stream) != cudaSuccess)
+                    return GBQR_ECUDA;
+                TRY(gemv_n(w.ex, N, k, V, N, hd, 1.0, 0.0, dvec, w.gs.partial, w.gs.partial_elems));
+                double ratio = 0.0;
+                TRY(step_ratio(dvec + m, &ratio));
+                if (!(ratio == ratio)) break;
+                TRY(axpby(w.ex, n, 1.0, dvec + m, 1.0, x));
+                TRY(axpby(w.ex, m, alpha, dvec, 1.0, r));        // back to r = a (r / a)
+                ++iters;
+                gmres_steps += k;
+                last = ratio;
+                TRY(backward_error(&eta));
+                if (ratio <= 1e-16) break;
+            }
         }
+    } else {
+        TRY(backward_error(&eta));
     }
+    const bool converged = (prec == GBQR_FP64) || eta <= eta_tol;   // FP64: eta is reported only
     long long rk = -1;
     if (cudaMemcpyAsync(&rk, &di->rankdef, sizeof rk, cudaMemcpyDeviceToHost, cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
@@ -866,6 +1010,8 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
         info->rankdef_col = rk;
         info->refine_iters = iters;
         info->refine_last = last;
+        info->gmres_steps = gmres_steps;
+        info->backward_err = eta;
     }
     if (rk >= 0) return GBQR_ERANKDEF;
     return converged ? GBQR_OK : GBQR_ENOCONV;

@@ -123,6 +123,35 @@ __global__ void __launch_bounds__(kThreads) norms2_kernel(int64_t n, const doubl
     }
 }
 
+// colsq[j] = sum_i A(i, j)^2: one warp per column.
+__global__ void __launch_bounds__(kThreads) colsq_kernel(int64_t m, int64_t n, const double *A, int64_t lda,
+                                                        double *colsq) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    double acc = 0.0;
+    for (int64_t i = lane; i < m; i += 32) acc = fma(A[i + j * lda], A[i + j * lda], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) colsq[j] = acc;
+}
+
+// out[0] = sum x (one CTA, fixed order)
+__global__ void __launch_bounds__(kThreads) sum_kernel(int64_t n, const double *x, double *out) {
+    __shared__ double red[kThreads / 32];
+    double a = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a += x[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        out[0] = s;
+    }
+}
+
 // y = a * x + b * y (elementwise)
 __global__ void __launch_bounds__(kThreads) axpby_kernel(int64_t n, double a, const double *x, double b, double *y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -364,6 +393,17 @@ gbqr_status norms2(const Exec &ex, int64_t n, const double *x, const double *y, 
     trace_begin(ex, FAM_OTHER);
     norms2_kernel<<<1, kThreads, 0, ex.stream>>>(n, x, y, out);
     return trace_end(ex, FAM_OTHER, 4.0 * n, 16.0 * n);
+}
+
+gbqr_status frob2(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, double *colsq, double *out) {
+    if (n <= 0) return GBQR_OK;
+    const int per = kThreads / 32;
+    trace_begin(ex, FAM_OTHER);
+    colsq_kernel<<<(unsigned)((n + per - 1) / per), kThreads, 0, ex.stream>>>(m, n, A, lda, colsq);
+    TRY_ST(trace_end(ex, FAM_OTHER, 2.0 * m * n, 8.0 * m * n));
+    trace_begin(ex, FAM_OTHER);
+    sum_kernel<<<1, kThreads, 0, ex.stream>>>(n, colsq, out);
+    return trace_end(ex, FAM_OTHER, (double)n, 8.0 * n);
 }
 
 gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y) {

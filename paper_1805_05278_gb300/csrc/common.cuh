@@ -150,6 +150,8 @@ gbqr_status gemv_t(const Exec &ex, int64_t m, int64_t n, const double *A, int64_
 gbqr_status norms2(const Exec &ex, int64_t n, const double *x, const double *y, double *out);
 // y = op(T) w for k x k upper triangular T (k <= 256)
 gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool trans, const double *w, double *y);
+// out[0] = ||A||_F^2 (m x n); colsq: n doubles of scratch.  Fixed order.
+gbqr_status frob2(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, double *colsq, double *out);
 // y = a x + b y
 gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y);
 

@@ -82,6 +82,22 @@ def ls_problem(m: int, n: int, decades: float, seed: int, noise: float = 1e-8):
     return a, x_true, b
 
 
+def ls_problem_kappa(m: int, n: int, kappa: float, seed: int, noise: float = 1e-8):
+    """Least-squares problem with prescribed singular values: A = Q1 diag(s)
+    Q2^T with Q1 (m x n) and Q2 (n x n) orthonormal products of random
+    reflectors and s_j = kappa^(-j/(n-1)) (so kappa_2(A) = kappa exactly and
+    no column scaling carries the ill-conditioning).  x_true iid N(0,1),
+    b = A x_true + noise * N(0,1).  Returns (A, x_true, b)."""
+    q1 = random_reflector_product(m, n, seed)
+    q2 = random_reflector_product(n, n, seed + 1)
+    s = kappa ** (-np.arange(n, dtype=np.float64) / max(n - 1, 1))
+    a = np.asfortranarray((q1 * s[None, :]) @ q2.T)
+    rng = np.random.default_rng(seed + 2)
+    x_true = rng.standard_normal(n)
+    b = a @ x_true + noise * rng.standard_normal(m)
+    return a, x_true, b
+
+
 @dataclass(frozen=True)
 class Workload:
     """One named workload: A (m x n) and an optional right-hand side b."""
