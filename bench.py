@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--batched-streams", type=int, default=0)
     p.add_argument("--batched-cutoff", type=int, default=0)
     p.add_argument("--serving", type=int, default=200, help="requests per serving run (0: skip)")
-    p.add_argument("--serving-rates", default="100,400,1600")
+    p.add_argument("--serving-rates", default="100,400,1600,5000")
     p.add_argument("--serving-workers", type=int, default=16)
     return p.parse_args()
 
@@ -118,13 +118,22 @@ def measure_serving(gb, dev, args):
             makespan = max(r.latency_ms / 1e3 + arrivals[i] for i, r in enumerate(results))
             lat = sorted(r.latency_ms for r in results)
             bad = sum(1 for r in results if r.status != gb.GBQR_OK)
-            fell_back = sum(1 for r in results if prec == gb.GBQR_PREC_AUTO and r.prec_used == gb.GBQR_FP64)
+            ran_mixed = sum(1 for r in results if r.prec_used != gb.GBQR_FP64)
             res_mode[str(int(rate))] = {"solves_per_s": len(results) / makespan,
                                         "p50_ms": lat[len(lat) // 2],
                                         "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                                        "failed": bad, "fp64_fallbacks": fell_back}
-        errs = [float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)) for x, (a, xt, b) in zip(xs, probs)]
-        res_mode["max_rel_err_vs_xtrue"] = max(errs)
+                                        "failed": bad, "ran_mixed": ran_mixed,
+                                        "ran_fp64": len(results) - ran_mixed,
+                                        "fell_back_to_fp64": sum(1 for r in results if r.fell_back)}
+        if mode == "fp64":
+            x_fp64 = [x.clone() for x in xs]
+        else:
+            # the AUTO result against the FP64 result of the same request,
+            # scaled by the conditioning bound kappa u (kappa = 10^d graded)
+            d = [float(torch.linalg.norm(x - x0) / torch.linalg.norm(x0)) for x, x0 in zip(xs, x_fp64)]
+            res_mode["max_rel_diff_vs_fp64"] = max(d)
+            res_mode["max_rel_diff_over_kappa_u"] = max(v / (10.0 ** sp[2] * 2.0 ** -53) for v, sp in zip(d, specs))
+            res_mode["max_rel_diff_vs_fp64_kappa_le_1e2"] = max([v for v, sp in zip(d, specs) if sp[2] <= 2.0] or [0.0])
         ctx.stop_serving()
         ctx.close()
         out[mode] = res_mode

@@ -80,8 +80,8 @@ typedef enum {
     GBQR_MIXED_BF16 = 1,    /* reserved: tensor-core update GEMMs + refinement */
     GBQR_MIXED_SPLITBF16 = 2,
     GBQR_FP32 = 3,
-    GBQR_PREC_AUTO = 4      /* serving: mixed for large problems (n > 256, m n^2 >= 4e9),
-                               FP64 otherwise, FP64 again when refinement stalls */
+    GBQR_PREC_AUTO = 4      /* serving: mixed for large problems (n >= 512, m n^2 >= 1.5e10),
+                               FP64 otherwise, FP64 again when refinement fails */
 } gbqr_prec;
 
 /* FP64 GEMM engine (gbqr_opts.fp64_gemm). */
@@ -357,7 +357,7 @@ typedef struct {
     int32_t state;         /* gbqr_req_state */
     int32_t status;        /* gbqr_status of the solve (when done) */
     int32_t prec_used;     /* the precision that produced x */
-    int32_t pad;
+    int32_t fell_back;     /* 1: GBQR_PREC_AUTO ran mixed, missed the target, re-ran FP64 */
     int64_t refine_iters;
     double queue_ms;       /* submit -> admitted */
     double run_ms;         /* admitted -> done */

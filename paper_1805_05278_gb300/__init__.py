@@ -57,7 +57,7 @@ class gbqr_request(ctypes.Structure):
 
 class gbqr_result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("prec_used", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("refine_iters", ctypes.c_int64), ("queue_ms", ctypes.c_double),
+                ("fell_back", ctypes.c_int32), ("refine_iters", ctypes.c_int64), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
                 ("tag", ctypes.c_uint64)]
 

@@ -36,16 +36,19 @@ struct Record {
     int state = GBQR_REQ_QUEUED;
     gbqr_status status = GBQR_OK;
     int prec_used = GBQR_FP64;
+    bool fell_back = false;
     int64_t iters = 0;
     Clock::time_point t_submit, t_start, t_done;
 };
 
 // GBQR_PREC_AUTO: the tensor-core updates only pay off where the trailing
-// update GEMMs dominate (at least three 128-wide panels and m n^2 >= 4e9);
-// smaller problems are bound by the FP64 panel factorizations, where the
-// mixed path would only add refinement steps.
+// update GEMMs dominate the solve.  Measured single-solve times (graded
+// columns, kappa ~ 1e4): mixed / FP64 = 1.5x faster at 65536 x 1024, 1.19x at
+// 16384 x 1024, even at 65536 x 512 (m n^2 = 1.7e10), slower below (the
+// FP64 panel factorizations dominate and the refinement adds its GMRES
+// steps; with n <= 128 there is no trailing update at all).
 int auto_precision(int64_t m, int64_t n) {
-    return (n > 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
+    return (n >= 512 && (double)m * n * n >= 1.5e10) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
 }
 
 // Workspace of gbqr_ls_solve for this request: its shape and precision, with
@@ -115,6 +118,7 @@ void worker_loop(gbqr_server *sv, int wi) {
         gbqr_status status = GBQR_OK;
         int64_t iters = 0;
         int used = r.prec;
+        bool fell_back = false;
         void *ws = nullptr;
         if (cudaMallocAsync(&ws, rec->footprint, st) != cudaSuccess) {
             cudaGetLastError();
@@ -128,6 +132,7 @@ void worker_loop(gbqr_server *sv, int wi) {
             iters = info.refine_iters;
             if (r.prec == GBQR_PREC_AUTO && status == GBQR_ENOCONV) {
                 used = GBQR_FP64;
+                fell_back = true;
                 status = gbqr_ls_solve(cx, r.m, r.n, r.A, r.lda, r.b, r.x, GBQR_FP64, &info);
             }
             gbqr_set_workspace(cx, nullptr, 0);
@@ -139,6 +144,7 @@ void worker_loop(gbqr_server *sv, int wi) {
             rec->status = status;
             rec->iters = iters;
             rec->prec_used = used;
+            rec->fell_back = fell_back;
             rec->t_done = Clock::now();
             rec->state = GBQR_REQ_DONE;
             sv->in_use -= rec->footprint;
@@ -246,6 +252,7 @@ GBQR_API gbqr_status gbqr_poll(gbqr_ctx *ctx, uint64_t id, int wait, gbqr_result
     if (r.state == GBQR_REQ_DONE) {
         out->status = r.status;
         out->prec_used = r.prec_used;
+        out->fell_back = r.fell_back ? 1 : 0;
         out->refine_iters = r.iters;
         out->queue_ms = ms_between(r.t_submit, r.t_start);
         out->run_ms = ms_between(r.t_start, r.t_done);
