@@ -43,6 +43,13 @@ SM_MAX_MHZ = 2070.0
 # Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 FMA) x 2.070 GHz.
 FP64_FLOP_PER_CLK_PER_SM = 4.0
 FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM bytes per dgemm launch (read + write, averaged over every launch of
+# one step) from an ncu capture of this exact configuration; the roofline's
+# traffic is null for any configuration without a capture.
+DGEMM_TRAFFIC_PER_LAUNCH = {
+    # (workload, panel_nb, cutoff_b, fanout, leaf_rows, lookahead, engine): bytes
+    ("graded_8192x8192", 64, 16, 8, 0, 1, "dfma"): 21.73e6,
+}
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs peak; LS solves/s, p99 ms: mixed vs FP64"
 
 
@@ -70,6 +77,7 @@ def parse():
     p.add_argument("--ls-solves", type=int, default=3, help="timed least-squares solves per grid point and precision (0: skip)")
     p.add_argument("--ls-decades", default="2,6,10", help="column-grading decades (kappa ~ 10^d x kappa(Gaussian))")
     p.add_argument("--ls-shapes", default="32768x2048,8192x8192")
+    p.add_argument("--no-ls-kappa", action="store_true", help="skip the condition estimate (torch.linalg)")
     p.add_argument("--batched", type=int, default=2000, help="matrices in the batched measurement (0: skip)")
     p.add_argument("--batched-steps", type=int, default=3)
     p.add_argument("--batched-streams", type=int, default=0)
@@ -232,7 +240,7 @@ def measure_ls(gb, ctx, dev, args):
             Tf = gb.colmajor(min(gb.default_panel_nb(m, n), n), n, devs)
             ctx.factor(Af, Tf, gb.GBQR_T_PANEL)
             torch.cuda.synchronize()
-            kappa = kappa_estimate(torch.triu(Af[:n, :n]))
+            kappa = None if args.no_ls_kappa else kappa_estimate(torch.triu(Af[:n, :n]))
             del Af, Tf
             row = {"m": m, "n": n, "decades": d, "kappa_est": kappa, "seed": seed}
             xs = {}
@@ -507,10 +515,15 @@ def run_gbqr(args):
         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
         "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.070 GHz (nominal 1.25 TFLOP/s FP64)",
-        "traffic": None,
+        "traffic": DGEMM_TRAFFIC_PER_LAUNCH.get(
+            (w.name, nb if layout == gb.GBQR_T_PANEL else 0, o.cutoff_b or 16, o.fanout or 8, o.leaf_rows,
+             o.lookahead or 1, "dmma" if o.fp64_gemm == gb.GBQR_GEMM_DMMA else "dfma")),
+        "traffic_unit": "bytes per launch (dram read + write, ncu)",
+        "algorithmic_bytes_per_launch": (gemm["bytes"] / gemm["launches"]) if gemm.get("launches") else None,
         "launches": gemm.get("launches"), "share_of_step": (gemm.get("ms", 0.0) / ms_total) if ms_total else None,
     }
     fams = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                "algorithmic_bytes_per_step": v["bytes"] / args.steps,
                 "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else None} for k, v in trace.items()}
 
     cpu = None
