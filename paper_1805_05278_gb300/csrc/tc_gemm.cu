@@ -217,23 +217,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const bool ok = mbar_wait(done, 0u, p.err);
         tc_fence_after();
         const int m = m0 + row;
+        // Each thread owns one row of the tile: per 32-column chunk, all 32 C
+        // loads are issued before any store, so a warp keeps 32 coalesced
+        // 256-byte loads in flight (one at a time, the FP64 read-modify-write
+        // of C is latency-bound at a few GB/s per SM).
 #pragma unroll 1
         for (int chunk = 0; chunk < BN / 32; ++chunk) {
             uint32_t v[32];
             if (total > 0) tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(chunk * 32), v);
             if (!ok || m >= p.M) continue;
+            const int nbase = n0 + chunk * 32;
+            const int cnt = min(32, p.N - nbase);
+            if (cnt <= 0) continue;
+            if (p.partial) {
+                float *pp = p.partial + (size_t)z * p.M * p.N + m + (size_t)nbase * p.M;
 #pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const int n = n0 + chunk * 32 + c;
-                if (n >= p.N) break;
-                const float d = (total > 0) ? __uint_as_float(v[c]) : 0.0f;
-                if (p.partial) {
-                    p.partial[(size_t)z * p.M * p.N + m + (size_t)n * p.M] = d;
-                } else {
-                    double *cp = p.C + m + (size_t)n * p.ldc;
-                    double out = p.alpha * (double)d;
-                    if (p.beta != 0.0) out = fma(p.beta, *cp, out);
-                    *cp = out;
+                for (int c = 0; c < 32; ++c)
+                    if (c < cnt) pp[(size_t)c * p.M] = (total > 0) ? __uint_as_float(v[c]) : 0.0f;
+            } else {
+                double *cp = p.C + m + (size_t)nbase * p.ldc;
+                double cv[32];
+#pragma unroll
+                for (int c = 0; c < 32; ++c) cv[c] = (p.beta != 0.0 && c < cnt) ? cp[(size_t)c * p.ldc] : 0.0;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    if (c < cnt) {
+                        const double d = (total > 0) ? (double)__uint_as_float(v[c]) : 0.0;
+                        double out = p.alpha * d;
+                        if (p.beta != 0.0) out = fma(p.beta, cv[c], out);
+                        cp[(size_t)c * p.ldc] = out;
+                    }
                 }
             }
         }
@@ -395,7 +408,9 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
     const int64_t tm = (op.M + TC_BM - 1) / TC_BM, tn = (op.N + BN - 1) / BN;
     const int ktiles = (int)((K + TC_BK - 1) / TC_BK);
     int S = 1;
-    if (tm * tn < ex.num_sms) S = (int)std::min<int64_t>({(ex.num_sms + tm * tn - 1) / (tm * tn), (int64_t)ktiles, 16});
+    // split K until the grid covers the SMs (the partials are summed in a
+    // fixed order by tc_reduce_kernel, so the result does not depend on timing)
+    if (tm * tn < ex.num_sms) S = (int)std::min<int64_t>({(ex.num_sms + tm * tn - 1) / (tm * tn), (int64_t)ktiles, 64});
     while (S > 1 && (size_t)S * op.M * op.N > partial_cap) --S;
     const int per = (ktiles + S - 1) / S;
     S = (ktiles + per - 1) / per;   // every split gets at least one K tile
