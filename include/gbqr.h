@@ -10,7 +10,8 @@
  *
  * Conventions shared by every call:
  *   - Real FP64, column-major: element (i, j) of a matrix X with leading
- *     dimension ldx is X[i + j*ldx].  m >= n >= 0 (Section 2.1).
+ *     dimension ldx is X[i + j*ldx].  m >= n >= 0 (Section 2.1), except
+ *     that gbqr_factor also takes wide matrices (m < n).
  *   - Matrix pointers are device pointers unless a call says otherwise.  The
  *     caller owns every matrix; the library only borrows the pointers for the
  *     duration of the stream-ordered work it enqueues.
@@ -165,9 +166,10 @@ GBQR_API gbqr_status gbqr_sync(gbqr_ctx *ctx, gbqr_info *info);
 
 /* ---- factorization (Algorithm 2 with TSQR base case) -------------------- */
 
-/* QR-factor the m x n matrix A (m >= n) in place.
+/* QR-factor the m x n matrix A in place.
  *   A   (m x n, lda):  in: A.  out: V's strict lower trapezoid and R's upper
  *                      triangle (Householder representation, Section 2.3).
+ *                      m >= n except for the wide case below.
  *   T   (ldt x n):     out: the kernel T in `t_layout` (GBQR_T_FULL: n x n,
  *                      ldt >= n, zeros written below the diagonal;
  *                      GBQR_T_PANEL: nb x n, ldt >= nb, nb = opts->panel_nb or
@@ -181,7 +183,13 @@ GBQR_API gbqr_status gbqr_sync(gbqr_ctx *ctx, gbqr_info *info);
  * A and T may instead both be HOST pointers (pageable or pinned): the call
  * then stages them through device workspace, copies the results back and
  * returns after the stream has synchronised.
- * Errors: EINVAL (m < n, lda < m, ldt too small, bad opts), ENOMEM, ECUDA. */
+ * Wide A (m < n, Section 2.1): the leading m x m block is factored as above
+ * and the m reflectors are applied to the remaining n - m columns, giving
+ * R = [R1, Q^T A2] (upper trapezoidal) over A; T then holds the min(m, n) = m
+ * reflectors' kernel (FULL: m x m; PANEL: nb x m), and apply_qt / apply_q /
+ * form_q take n = m.  Device pointers only for wide A (host: EUNSUPPORTED).
+ * Errors: EINVAL (lda < m, ldt too small, bad opts), ENOMEM, ECUDA,
+ * EUNSUPPORTED. */
 GBQR_API gbqr_status gbqr_factor(gbqr_ctx *ctx, int64_t m, int64_t n, double *A, int64_t lda,
                         double *T, int64_t ldt, int t_layout, const gbqr_opts *opts);
 

@@ -82,13 +82,16 @@ class Oracle:
 
     def house_qr(self, a: np.ndarray, nsteps: int | None = None):
         """Returns (VR, tau): V (strict lower, unit diagonal implied) and R
-        (upper triangle) packed in one m x n array, and the n scalings."""
+        (upper triangle, upper trapezoidal when m < n) packed in one m x n
+        array, and the min(m, n) scalings (Section 2.1; m < n by splitting
+        off the leading square block)."""
         vr = _fortran(a)
         m, n = vr.shape
-        tau = np.zeros(max(n, 1))
-        k = n if nsteps is None else nsteps
+        kmax = min(m, n)
+        tau = np.zeros(max(kmax, 1))
+        k = kmax if nsteps is None else min(nsteps, kmax)
         self._check(self.lib.orc_house_qr(m, n, _ptr(vr), max(m, 1), _ptr(tau), k), "house_qr")
-        return vr, tau[:n]
+        return vr, tau[:kmax]
 
     def larft(self, vr: np.ndarray, tau: np.ndarray) -> np.ndarray:
         vr = _fortran(vr)

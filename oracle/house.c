@@ -69,13 +69,17 @@ static double nrm2(long n, const double *x)
     return amax * sqrt(s);
 }
 
-/* Householder QR of the m x n matrix A (m >= n), first nsteps reflectors.
- * nsteps < n leaves a partial factorization: columns 0..nsteps-1 hold V\R and
- * columns nsteps..n-1 hold H_{nsteps-1} ... H_0 A(:, nsteps:n). */
+/* Householder QR of the m x n matrix A, first nsteps <= min(m, n)
+ * reflectors.  nsteps < min(m, n) leaves a partial factorization: columns
+ * 0..nsteps-1 hold V\R and columns nsteps..n-1 hold
+ * H_{nsteps-1} ... H_0 A(:, nsteps:n).  With m < n the m reflectors of the
+ * leading m x m block are applied to every column, which is the wide-matrix
+ * construction of Section 2.1: A = [A1 A2], A1 = Q R1, R = [R1, Q^T A2]. */
 int orc_house_qr(long m, long n, double *a, long lda, double *tau, long nsteps)
 {
-    if (m < 0 || n < 0 || lda < (m > 1 ? m : 1) || m < n) return 1;
+    if (m < 0 || n < 0 || lda < (m > 1 ? m : 1)) return 1;
     if (nsteps > n) nsteps = n;
+    if (nsteps > m) nsteps = m;
     for (long j = 0; j < nsteps; ++j) {
         double alpha = AT(a, j, j, lda);
         double xnorm = nrm2(m - j - 1, &AT(a, j + 1, j, lda));

@@ -119,7 +119,8 @@ struct Layout {
     TsqrPlan tsqr;
 };
 
-Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num_sms, bool staging = true) {
+Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num_sms, bool staging = true,
+                   size_t min_M = 0) {
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 16), 256); return o; };
@@ -132,6 +133,7 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     size_t nM = (size_t)((n + 1) / 2) * (size_t)(n / 2 + 1);
     nM = std::max(nM, (size_t)nb * (size_t)std::max<int64_t>(n, 1));
     if (t_layout == GBQR_T_FULL) nM = std::max(nM, (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1));
+    nM = std::max(nM, min_M);   // e.g. Q^T A2 of a wide matrix
     L.n_M = nM;
     L.n_bigA = staging ? (size_t)std::max<int64_t>(m, 1) * (size_t)std::max<int64_t>(n, 1) : 1;
     L.n_bigT = staging ? (size_t)std::max<int64_t>(n, 1) * (size_t)std::max<int64_t>(n, 1) : 1;
@@ -355,9 +357,10 @@ gbqr_status zero_counters(const Work &w, cudaStream_t s) {
     return GBQR_OK;
 }
 
-gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const Params &pr, Work *w) {
+gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const Params &pr, Work *w,
+                       size_t min_M = 0) {
     if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
-    const Layout L = make_layout(m, n, t_layout, pr, cx->num_sms);
+    const Layout L = make_layout(m, n, t_layout, pr, cx->num_sms, true, min_M);
     gbqr_status st = ensure_workspace(cx, L.total);
     if (st != GBQR_OK) return st;
     carve_work(cx, cx->ws, L, pr, cx->exec(), w);
@@ -682,7 +685,7 @@ gbqr_status gbqr_set_workspace(gbqr_ctx *cx, void *ptr, size_t bytes) {
 }
 
 size_t gbqr_workspace_bytes(int64_t m, int64_t n, int t_layout, const gbqr_opts *opts) {
-    if (m < 0 || n < 0 || m < n) return 0;
+    if (m < 0 || n < 0) return 0;
     if (t_layout != GBQR_T_FULL && t_layout != GBQR_T_PANEL) return 0;
     Params pr;
     if (!resolve(opts, m, n, &pr)) return 0;
@@ -691,6 +694,11 @@ size_t gbqr_workspace_bytes(int64_t m, int64_t n, int t_layout, const gbqr_opts 
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) { cudaGetLastError(); sms = 152; }
     } else {
         cudaGetLastError();
+    }
+    if (n > m) {   // wide: the leading m x m block, then Q^T A2
+        const int64_t nbp = std::min<int64_t>(pr.nb, std::max<int64_t>(m, 1));
+        return make_layout(m, m, t_layout, pr, sms, true,
+                           (size_t)(t_layout == GBQR_T_FULL ? m : nbp) * (size_t)(n - m)).total;
     }
     return make_layout(m, n, t_layout, pr, sms).total;
 }
@@ -727,6 +735,20 @@ gbqr_status gbqr::factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, 
     if (!cx) return GBQR_EINVAL;
     Params pr;
     if (!resolve(opts, m, n, &pr)) return GBQR_EINVAL;
+    if (m >= 0 && n > m) {
+        // Wide matrix (Section 2.1): A = [A1 A2] with square A1 = Q R1 by
+        // QR-EG, then R = [R1, Q^T A2] by applying the m reflectors to A2.
+        const int64_t k = m, nr = n - m;
+        TRY(check_layout_args(m, k, lda, ldt, t_layout, pr.nb));
+        if (k == 0) return GBQR_OK;
+        if (!A || !T) return GBQR_EINVAL;
+        if (is_host_pointer(A) || is_host_pointer(T)) return GBQR_EUNSUPPORTED;
+        const int64_t nbp = std::min<int64_t>(pr.nb, k);
+        Work w;
+        TRY(begin_work(cx, m, k, t_layout, pr, &w, (size_t)(t_layout == GBQR_T_FULL ? k : nbp) * (size_t)nr));
+        TRY(factor_device(w, m, k, A, lda, T, ldt, t_layout));
+        return apply_q_any(w, true, m, k, A, lda, T, ldt, t_layout, nbp, nr, A + (size_t)k * lda, lda, false);
+    }
     TRY(check_layout_args(m, n, lda, ldt, t_layout, pr.nb));
     if (n == 0) return GBQR_OK;
     if (!A || !T) return GBQR_EINVAL;

@@ -253,8 +253,33 @@ def pin_partial_steps(orc):
     assert np.max(np.abs(vr_part[:, k:] - rest)) <= 1e-13 * np.linalg.norm(a)
 
 
+def pin_wide(orc):
+    """m < n (Section 2.1): R = [R1, Q^T A2] with A1 = Q R1.  Pinned to LAPACK's
+    dgeqrf of the wide matrix element by element (up to the empty-subcolumn
+    reflector of row m-1: LAPACK tau = 0, the sign reading tau = 2, which
+    negates row m-1 of R), to A = Q R with the explicit reflector product,
+    and to R^T R = A^T A."""
+    for (m, n, seed) in [(5, 9, 61), (20, 47, 62), (64, 65, 63)]:
+        a = workloads.gaussian(m, n, seed)
+        vr, tau = orc.house_qr(a)
+        assert vr.shape == (m, n) and tau.shape == (m,)
+        h, tl = np.linalg.qr(a, mode="raw")
+        h = np.array(h.T, order="F")
+        assert tl[-1] == 0.0 and tau[-1] == 2.0
+        tl = tl.copy()
+        tl[-1] = 2.0
+        h[m - 1, m - 1:] = -h[m - 1, m - 1:]
+        assert np.max(np.abs(tau - tl)) <= 1e-13
+        assert np.max(np.abs(np.tril(vr[:, :m], -1) - np.tril(h[:, :m], -1))) <= 1e-12
+        r = np.triu(vr)
+        assert np.max(np.abs(r - np.triu(h))) <= 1e-12 * np.max(np.abs(a)) * m
+        q = explicit_q(vr[:, :m], tau)
+        assert np.linalg.norm(a - q @ r) / np.linalg.norm(a) <= 1e-14 * n
+        assert np.linalg.norm(r.T @ r - a.T @ a) / np.linalg.norm(a.T @ a) <= 1e-14 * n
+
+
 ALL_PINS = [
     pin_gram_schmidt_tiny, pin_cholesky, pin_lapack_elementwise, pin_orthogonal_input,
     pin_upper_triangular, pin_zero_column, pin_single_column, pin_reflectors, pin_backward_error,
-    pin_t_two_ways, pin_apply, pin_ls, pin_trsv, pin_partial_steps,
+    pin_t_two_ways, pin_apply, pin_ls, pin_trsv, pin_partial_steps, pin_wide,
 ]

@@ -55,7 +55,7 @@ def test_strerror(lib):
 
 def test_workspace_query(lib):
     import paper_1805_05278_gb300 as gb
-    assert gb.gbqr_workspace_bytes(10, 20, gb.GBQR_T_FULL, None) == 0          # m < n
+    assert gb.gbqr_workspace_bytes(10, 20, gb.GBQR_T_FULL, None) > 0           # wide (Section 2.1)
     assert gb.gbqr_workspace_bytes(-1, 0, gb.GBQR_T_FULL, None) == 0
     assert gb.gbqr_workspace_bytes(100, 10, 7, None) == 0                     # bad layout
     bad = gb.opts(cutoff_b=65)

@@ -147,7 +147,14 @@ def test_invalid_arguments(gb, ctx):
     T = gb.colmajor(20, 20)
     h = ctx.handle
     P = ctypes.c_void_p
-    assert gb.gbqr_factor(h, 10, 20, P(A.data_ptr()), 10, P(T.data_ptr()), 20, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
+    # wide: lda < m and ldt < min(m, n) are rejected; host pointers are not supported
+    assert gb.gbqr_factor(h, 10, 20, P(A.data_ptr()), 9, P(T.data_ptr()), 20, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
+    assert gb.gbqr_factor(h, 10, 20, P(A.data_ptr()), 10, P(T.data_ptr()), 9, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
+    import numpy as _np
+    ah = _np.zeros((10, 20), order="F")
+    th = _np.zeros((10, 10), order="F")
+    assert gb.gbqr_factor(h, 10, 20, P(ah.ctypes.data), 10, P(th.ctypes.data), 10, gb.GBQR_T_FULL,
+                          None) == gb.GBQR_EUNSUPPORTED
     A = gb.colmajor(30, 20)
     assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 29, P(T.data_ptr()), 20, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
     assert gb.gbqr_factor(h, 30, 20, P(A.data_ptr()), 30, P(T.data_ptr()), 19, gb.GBQR_T_FULL, None) == gb.GBQR_EINVAL
@@ -200,3 +207,33 @@ def test_fp64_gemm_engine_rejects_unknown(gb, ctx):
     a = workloads.gaussian(100, 40, 1)
     with pytest.raises(gb.GbqrError):
         _gpu.factor_gpu(ctx, a, gb.GBQR_T_FULL, gb.opts(fp64_gemm=7))
+
+
+@pytest.mark.parametrize("m,n,layout_name", [(100, 250, "full"), (100, 250, "panel"), (700, 1500, "panel"),
+                                             (2000, 3100, "full"), (33, 34, "panel"), (1, 5, "full")])
+def test_wide_matrix(gb, ctx, orc, m, n, layout_name):
+    """m < n (Section 2.1): A = [A1 A2], A1 = Q R1 by QR-EG, R = [R1, Q^T A2];
+    V, R (upper trapezoidal) and the m reflectors' T match the oracle."""
+    import torch
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    a = workloads.gaussian(m, n, 300 + m)
+    nb = gb.default_panel_nb(m, m)
+    A = _gpu.device_matrix(a)
+    T = gb.colmajor(m if layout == gb.GBQR_T_FULL else min(nb, m), m, fill=float("nan"))
+    ctx.factor(A, T, layout)
+    torch.cuda.synchronize()
+    VR, Tg = gb.to_numpy(A), gb.to_numpy(T)
+    vr_o, tau_o = orc.house_qr(a)
+    assert np.max(np.abs(np.tril(VR[:, :m], -1) - np.tril(vr_o[:, :m], -1))) <= _gpu.TOL_V
+    r, r_o = np.triu(VR), np.triu(vr_o)
+    colnorm = np.linalg.norm(a, axis=0)
+    assert np.max(np.linalg.norm(r - r_o, axis=0) / colnorm) <= _gpu.TOL_R_COL
+    t_o = orc.larft(vr_o[:, :m], tau_o)
+    if layout == gb.GBQR_T_PANEL:
+        t_o = _gpu.panel_blocks_of(t_o, nb)
+    assert np.max(np.abs(Tg - t_o)) / max(1.0, np.max(np.abs(t_o))) <= _gpu.TOL_T
+    # the factors apply: Q^T A = R through gbqr_apply_qt with n = m reflectors
+    B = _gpu.device_matrix(a)
+    ctx.apply_qt(A[:, :m], T, B, layout, nb)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(gb.to_numpy(B) - r) / np.linalg.norm(a) <= _gpu.TOL_BACKWARD
