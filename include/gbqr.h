@@ -215,6 +215,18 @@ GBQR_API gbqr_status gbqr_factor_batched(gbqr_ctx *ctx, int count, const int64_t
                                          double *const *A, const int64_t *lda, double *const *T,
                                          const int64_t *ldt, const gbqr_opts *opts);
 
+/* The same batch in FP32: A[i], T[i] are float, and every step - the TSQR
+ * leaves, merges, reconstruction and the QR-EG update and T-assembly products
+ * - computes in FP32 with the same kernels instantiated for float (this part
+ * issues FP32 at 64x its FP64 rate, and the TSQR reflector chains shorten
+ * accordingly).  Same layout, scheduling, streams, workspace and graph
+ * capture rules as gbqr_factor_batched; opts->update_prec must be GBQR_FP64
+ * (meaning: no tensor-core updates) or zero; the autotuner's cache is not
+ * used.  Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_factor_batched_f32(gbqr_ctx *ctx, int count, const int64_t *m, const int64_t *n,
+                                             float *const *A, const int64_t *lda, float *const *T,
+                                             const int64_t *ldt, const gbqr_opts *opts);
+
 /* Workspace bytes gbqr_factor_batched needs for these shapes (0 if invalid). */
 GBQR_API size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *n, const gbqr_opts *opts);
 

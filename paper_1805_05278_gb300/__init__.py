@@ -86,6 +86,9 @@ SIGNATURES = {
     "gbqr_factor_batched": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                             ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
                                             ctypes.POINTER(_I64), ctypes.POINTER(gbqr_opts)]),
+    "gbqr_factor_batched_f32": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                                ctypes.POINTER(_P), ctypes.POINTER(_I64), ctypes.POINTER(_P),
+                                                ctypes.POINTER(_I64), ctypes.POINTER(gbqr_opts)]),
     "gbqr_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(_I64),
                                                        ctypes.POINTER(gbqr_opts)]),
     "gbqr_graph_begin": (ctypes.c_int, [_P]),
@@ -171,11 +174,12 @@ def opts_dict(o: gbqr_opts) -> dict:
     return {name: getattr(o, name) for name, _ in gbqr_opts._fields_}
 
 
-def _cm(x, name: str):
-    """(pointer, rows, cols, leading dimension) of a column-major float64 tensor."""
+def _cm(x, name: str, dtype=None):
+    """(pointer, rows, cols, leading dimension) of a column-major float64 (or
+    `dtype`) tensor."""
     import torch
-    if x.dtype != torch.float64:
-        raise TypeError(f"{name} must be float64")
+    if x.dtype != (torch.float64 if dtype is None else dtype):
+        raise TypeError(f"{name} must be {dtype or torch.float64}")
     if x.dim() == 1:
         return x.data_ptr(), x.shape[0], 1, max(1, x.shape[0])
     if x.dim() != 2 or (x.stride(0) != 1 and x.shape[0] > 1):
@@ -311,17 +315,22 @@ class Context:
 
     def factor_batched(self, As, Ts, o: gbqr_opts | None = None) -> int:
         """QR of every column-major matrix in As (in place); Ts[i] receives
-        the panel kernels (rows >= min(128, n_i))."""
+        the panel kernels (rows >= min(128, n_i)).  float32 matrices go to
+        gbqr_factor_batched_f32 (FP32 throughout), float64 ones to
+        gbqr_factor_batched."""
+        import torch
         cnt = len(As)
         I64 = _I64 * cnt
         Ps = _P * cnt
         ms, ns, ldas, ldts, pa, pt = I64(), I64(), I64(), I64(), Ps(), Ps()
+        dt = As[0].dtype if cnt else torch.float64
         for i, (A, T) in enumerate(zip(As, Ts)):
-            a_ptr, m, n, lda = _cm(A, "A")
-            t_ptr, _, _, ldt = _cm(T, "T")
+            a_ptr, m, n, lda = _cm(A, "A", dt)
+            t_ptr, _, _, ldt = _cm(T, "T", dt)
             ms[i], ns[i], ldas[i], ldts[i], pa[i], pt[i] = m, n, lda, ldt, a_ptr, t_ptr
-        return check(gbqr_factor_batched(self.handle, cnt, ms, ns, pa, ldas, pt, ldts,  # noqa: F821
-                                         ctypes.byref(o) if o is not None else None), "gbqr_factor_batched")
+        fn, nm = ((gbqr_factor_batched_f32, "gbqr_factor_batched_f32") if dt == torch.float32  # noqa: F821
+                  else (gbqr_factor_batched, "gbqr_factor_batched"))  # noqa: F821
+        return check(fn(self.handle, cnt, ms, ns, pa, ldas, pt, ldts, ctypes.byref(o) if o is not None else None), nm)
 
     # ---- autotuner
     def autotune(self, m: int, n: int, layout: int = GBQR_T_PANEL, prec: int = GBQR_FP64,

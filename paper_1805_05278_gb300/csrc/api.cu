@@ -16,6 +16,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <type_traits>
 #include <vector>
 
 using namespace gbqr;
@@ -283,6 +284,28 @@ struct Work {
     GemmScratch gs2;
     double *M1b, *M2b;
 
+    // Typed views of the workspace (regions are sized for FP64; an FP32 call
+    // uses the same bytes).
+    template <class Real> Real *m1() const { return reinterpret_cast<Real *>(M1); }
+    template <class Real> Real *m2() const { return reinterpret_cast<Real *>(M2); }
+    template <class Real> GemmScratchT<Real> gsr() const {
+        GemmScratchT<Real> g;
+        g.partial = reinterpret_cast<Real *>(gs.partial);
+        g.partial_elems = gs.partial_elems * (sizeof(double) / sizeof(Real));
+        g.counters = gs.counters;
+        g.ncounters = gs.ncounters;
+        return g;
+    }
+    template <class Real> TsqrWorkT<Real> twr() const {
+        TsqrWorkT<Real> t;
+        t.R = reinterpret_cast<Real *>(tw.R);
+        t.T = reinterpret_cast<Real *>(tw.T);
+        t.Y = reinterpret_cast<Real *>(tw.Y);
+        t.X = reinterpret_cast<Real *>(tw.X);
+        t.counters = tw.counters;
+        return t;
+    }
+
     // The second lane: same TSQR workspace, its own GEMM scratch and
     // temporaries, enqueued on the context's side stream.
     Work lane2() const {
@@ -371,11 +394,14 @@ gbqr_status begin_work(gbqr_ctx *cx, int64_t m, int64_t n, int t_layout, const P
 
 // C (mr x nc) <- (I - V op(T) V^T) C; op(T) = T^T when trans.  V is the unit
 // lower trapezoidal mr x kv basis, T the kv x kv upper triangular kernel.
+template <class Real>
 gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
-                        const double *V, int64_t ldv, const double *T, int64_t ldt, double *C, int64_t ldc,
+                        const Real *V, int64_t ldv, const Real *T, int64_t ldt, Real *C, int64_t ldc,
                         int nsplit = 0) {
     if (mr <= 0 || nc <= 0 || kv <= 0) return GBQR_OK;
     if ((size_t)kv * (size_t)nc > w.n_M) return GBQR_ENOMEM;
+    constexpr bool fp64 = std::is_same<Real, double>::value;
+    if constexpr (fp64) {
     if (nc == 1) {
         // one vector: matrix-vector products instead of 1-column GEMM tiles
         TRY(gemv_t(w.ex, mr, kv, V, ldv, C, 1.0, 0.0, w.M1, MASK_UNIT_LOWER));
@@ -409,85 +435,95 @@ gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
         u.B = w.M2; u.ldb = kv; u.C = C; u.ldc = ldc; u.alpha = -1.0; u.beta = 1.0; u.nsplit = nsplit;
         return tc_gemm(w.ex, u, w.tcs);
     }
-    GemmOp g;
+    }
+    Real *M1 = w.m1<Real>(), *M2 = w.m2<Real>();
+    const GemmScratchT<Real> gsr = w.gsr<Real>();
+    GemmOpT<Real> g;
     g.M = kv; g.N = nc; g.K = mr;
     g.A = V; g.lda = ldv; g.ta = true; g.maskA = MASK_UNIT_LOWER;
-    g.B = C; g.ldb = ldc; g.C = w.M1; g.ldc = kv;
-    TRY(gemm(w.ex, g, w.gs));
-    GemmOp h;
+    g.B = C; g.ldb = ldc; g.C = M1; g.ldc = kv;
+    TRY(gemm(w.ex, g, gsr));
+    GemmOpT<Real> h;
     h.M = kv; h.N = nc; h.K = kv;
     h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
-    h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
-    TRY(gemm(w.ex, h, w.gs));
-    GemmOp u;
+    h.B = M1; h.ldb = kv; h.C = M2; h.ldc = kv;
+    TRY(gemm(w.ex, h, gsr));
+    GemmOpT<Real> u;
     u.M = mr; u.N = nc; u.K = kv;
     u.A = V; u.lda = ldv; u.ta = false; u.maskA = MASK_UNIT_LOWER;
-    u.B = w.M2; u.ldb = kv; u.C = C; u.ldc = ldc; u.alpha = -1.0; u.beta = 1.0;
-    return gemm(w.ex, u, w.gs);
+    u.B = M2; u.ldb = kv; u.C = C; u.ldc = ldc; u.alpha = Real(-1); u.beta = Real(1);
+    return gemm(w.ex, u, gsr);
 }
 
 // Base case: TSQR of the m x n panel (n <= b).
-gbqr_status base_qr(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt) {
+template <class Real>
+gbqr_status base_qr(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, Real *T, int64_t ldt) {
     TsqrPlan pl;
     if (!tsqr_plan(m, (int)n, w.pr.leaf_rows, w.pr.fanout, w.ex.num_sms, &pl)) return GBQR_EINVAL;
     if (pl.nR > w.L.tsqr.nR || pl.nT > w.L.tsqr.nT || pl.nY > w.L.tsqr.nY || pl.ncount > w.L.tsqr.ncount)
         return GBQR_ENOMEM;
-    return tsqr_run(w.ex, pl, A, lda, T, ldt, w.tw);
+    return tsqr_run(w.ex, pl, A, lda, T, ldt, w.twr<Real>());
 }
 
 // Algorithm 2: (V, T, R) = QR-EG(A, b), V\R in place over A, T (n x n) at T.
-gbqr_status qr_eg(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt) {
+template <class Real>
+gbqr_status qr_eg(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, Real *T, int64_t ldt) {
     if (n <= 0) return GBQR_OK;
     if (n <= w.pr.b) return base_qr(w, m, n, A, lda, T, ldt);
     const int64_t n1 = n / 2, n2 = n - n1;
-    double *AR = A + n1 * lda;
+    Real *AR = A + n1 * lda;
+    Real *M1 = w.m1<Real>(), *M2 = w.m2<Real>();
+    const GemmScratchT<Real> gsr = w.gsr<Real>();
     TRY(qr_eg(w, m, n1, A, lda, T, ldt));                  // left recursion
     // M1 = V_L^T A_R ; M2 = T_L^T M1 ; A_R -= V_L M2
     TRY(apply_block(w, true, m, n2, n1, A, lda, T, ldt, AR, lda));
     // right recursion on B22
-    double *TR = T + n1 + n1 * ldt;
+    Real *TR = T + n1 + n1 * ldt;
     TRY(qr_eg(w, m - n1, n2, A + n1 + n1 * lda, lda, TR, ldt));
     // M3 = V_L(n1:m, :)^T V_R ; M4 = M3 T_R ; T12 = -T_L M4
     if ((size_t)n1 * (size_t)n2 > w.n_M) return GBQR_ENOMEM;
-    GemmOp g3;
+    GemmOpT<Real> g3;
     g3.M = n1; g3.N = n2; g3.K = m - n1;
     g3.A = A + n1; g3.lda = lda; g3.ta = true; g3.maskA = MASK_NONE;
     g3.B = A + n1 + n1 * lda; g3.ldb = lda; g3.maskB = MASK_UNIT_LOWER;
-    g3.C = w.M1; g3.ldc = n1;
-    TRY(gemm(w.ex, g3, w.gs));
-    GemmOp g4;
+    g3.C = M1; g3.ldc = n1;
+    TRY(gemm(w.ex, g3, gsr));
+    GemmOpT<Real> g4;
     g4.M = n1; g4.N = n2; g4.K = n2;
-    g4.A = w.M1; g4.lda = n1; g4.ta = false;
+    g4.A = M1; g4.lda = n1; g4.ta = false;
     g4.B = TR; g4.ldb = ldt; g4.maskB = MASK_UPPER;
-    g4.C = w.M2; g4.ldc = n1;
-    TRY(gemm(w.ex, g4, w.gs));
-    GemmOp g5;
+    g4.C = M2; g4.ldc = n1;
+    TRY(gemm(w.ex, g4, gsr));
+    GemmOpT<Real> g5;
     g5.M = n1; g5.N = n2; g5.K = n1;
     g5.A = T; g5.lda = ldt; g5.ta = false; g5.maskA = MASK_UPPER;
-    g5.B = w.M2; g5.ldb = n1;
-    g5.C = T + n1 * ldt; g5.ldc = ldt; g5.alpha = -1.0; g5.beta = 0.0;
-    return gemm(w.ex, g5, w.gs);
+    g5.B = M2; g5.ldb = n1;
+    g5.C = T + n1 * ldt; g5.ldc = ldt; g5.alpha = Real(-1); g5.beta = Real(0);
+    return gemm(w.ex, g5, gsr);
 }
 
 // Zero T(i, j) for i > (j mod nb) (the strict lower part of every block).
-__global__ void zero_below_blocks_kernel(int64_t rows, int64_t n, int64_t nb, double *T, int64_t ldt) {
+template <class Real>
+__global__ void zero_below_blocks_kernel(int64_t rows, int64_t n, int64_t nb, Real *T, int64_t ldt) {
     const int64_t total = rows * n;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e % rows, j = e / rows;
-        if (i > j % nb) T[i + j * ldt] = 0.0;
+        if (i > j % nb) T[i + j * ldt] = Real(0);
     }
 }
 
-gbqr_status zero_below_blocks(Work &w, int64_t rows, int64_t n, int64_t nb, double *T, int64_t ldt) {
+template <class Real>
+gbqr_status zero_below_blocks(Work &w, int64_t rows, int64_t n, int64_t nb, Real *T, int64_t ldt) {
     if (rows <= 1 || n <= 0) return GBQR_OK;
     trace_begin(w.ex, FAM_OTHER);
     const int64_t total = rows * n;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)w.ex.num_sms * 8));
-    zero_below_blocks_kernel<<<grid, 256, 0, w.ex.stream>>>(rows, n, nb, T, ldt);
-    return trace_end(w.ex, FAM_OTHER, 0.0, 4.0 * (double)total);
+    zero_below_blocks_kernel<Real><<<grid, 256, 0, w.ex.stream>>>(rows, n, nb, T, ldt);
+    return trace_end(w.ex, FAM_OTHER, 0.0, (double)sizeof(Real) / 2.0 * (double)total);
 }
 
-gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt, int layout) {
+template <class Real>
+gbqr_status factor_device(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, Real *T, int64_t ldt, int layout) {
     DeviceInfo *di = w.cx->dinfo;
     TRY(scan_nonfinite(w.ex, m, n, A, lda, &di->nonfinite));
     if (layout == GBQR_T_FULL) {
@@ -501,8 +537,8 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda,
     if (!w.pr.lookahead || npan == 1 || !cx->side) {
         for (int64_t j0 = 0; j0 < n; j0 += nb) {
             const int64_t wd = std::min<int64_t>(nb, n - j0);
-            double *Ap = A + j0 + j0 * lda;
-            double *Tk = T + j0 * ldt;
+            Real *Ap = A + j0 + j0 * lda;
+            Real *Tk = T + j0 * ldt;
             TRY(qr_eg(w, m - j0, wd, Ap, lda, Tk, ldt));
             if (j0 + wd < n)
                 TRY(apply_block(w, true, m - j0, n - j0 - wd, wd, Ap, lda, Tk, ldt, A + j0 + (j0 + wd) * lda, lda,
@@ -524,8 +560,8 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, double *A, int64_t lda,
         if (cudaStreamWaitEvent(ms, cx->ev_panel, 0) != cudaSuccess) return GBQR_ECUDA;   // panel k done
         if (k + 1 == npan) break;
         const int64_t j1 = j0 + wd, w1 = std::min<int64_t>(nb, n - j1);
-        const double *Vk = A + j0 + j0 * lda;
-        const double *Tk = T + j0 * ldt;
+        const Real *Vk = A + j0 + j0 * lda;
+        const Real *Tk = T + j0 * ldt;
         // panel k+1's columns first ...
         TRY(apply_block(w, true, m - j0, w1, wd, Vk, lda, Tk, ldt, A + j0 + j1 * lda, lda, w.pr.nsplit));
         if (cudaEventRecord(cx->ev_ready, ms) != cudaSuccess || cudaStreamWaitEvent(ss, cx->ev_ready, 0) != cudaSuccess)
@@ -1047,10 +1083,18 @@ gbqr_status gbqr_factor_batched(gbqr_ctx *cx, int count, const int64_t *m, const
                                         with_tuned(cx, GBQR_TUNE_BATCHED, 0, 0, GBQR_T_PANEL, opts, &eff, false));
 }
 
+gbqr_status gbqr_factor_batched_f32(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, float *const *A,
+                                    const int64_t *lda, float *const *T, const int64_t *ldt, const gbqr_opts *opts) {
+    if (!cx) return GBQR_EINVAL;
+    if (opts && opts->update_prec != GBQR_FP64) return GBQR_EINVAL;   // FP32 throughout
+    return gbqr::factor_batched_untuned(cx, count, m, n, A, lda, T, ldt, opts);
+}
+
 }  // extern "C"
 
-gbqr_status gbqr::factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, double *const *A,
-                                         const int64_t *lda, double *const *T, const int64_t *ldt, const gbqr_opts *opts,
+template <class Real>
+gbqr_status gbqr::factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, Real *const *A,
+                                         const int64_t *lda, Real *const *T, const int64_t *ldt, const gbqr_opts *opts,
                                          bool prepare_only) {
     if (!cx || count < 0) return GBQR_EINVAL;
     if (count == 0) return GBQR_OK;
@@ -1120,6 +1164,13 @@ gbqr_status gbqr::factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t 
     }
     return GBQR_OK;
 }
+
+template gbqr_status gbqr::factor_batched_untuned<double>(gbqr_ctx *, int, const int64_t *, const int64_t *,
+                                                          double *const *, const int64_t *, double *const *,
+                                                          const int64_t *, const gbqr_opts *, bool);
+template gbqr_status gbqr::factor_batched_untuned<float>(gbqr_ctx *, int, const int64_t *, const int64_t *,
+                                                         float *const *, const int64_t *, float *const *,
+                                                         const int64_t *, const gbqr_opts *, bool);
 
 extern "C" {
 

@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(kThreads) copy_kernel(int64_t m, int64_t n, co
     }
 }
 
-__global__ void __launch_bounds__(kThreads) nonfinite_kernel(int64_t m, int64_t n, const double *A, int64_t lda,
+template <class Real>
+__global__ void __launch_bounds__(kThreads) nonfinite_kernel(int64_t m, int64_t n, const Real *A, int64_t lda,
                                                            unsigned long long *flag) {
     const int64_t total = m * n;
     int bad = 0;
@@ -310,13 +311,18 @@ gbqr_status copy_matrix(const Exec &ex, int64_t m, int64_t n, const double *src,
     return trace_end(ex, FAM_OTHER, 0.0, 16.0 * m * n);
 }
 
-gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda,
+template <class Real>
+gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const Real *A, int64_t lda,
                            unsigned long long *flag) {
     if (m <= 0 || n <= 0) return GBQR_OK;
     trace_begin(ex, FAM_OTHER);
-    nonfinite_kernel<<<grid_for(m * n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, A, lda, flag);
-    return trace_end(ex, FAM_OTHER, 0.0, 8.0 * m * n);
+    nonfinite_kernel<Real><<<grid_for(m * n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, A, lda, flag);
+    return trace_end(ex, FAM_OTHER, 0.0, (double)sizeof(Real) * m * n);
 }
+template gbqr_status scan_nonfinite<double>(const Exec &, int64_t, int64_t, const double *, int64_t,
+                                            unsigned long long *);
+template gbqr_status scan_nonfinite<float>(const Exec &, int64_t, int64_t, const float *, int64_t,
+                                           unsigned long long *);
 
 gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef) {
     if (n <= 0) return GBQR_OK;

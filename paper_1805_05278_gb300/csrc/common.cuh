@@ -53,26 +53,33 @@ enum Mask {
 // C (M x N) = alpha * op(A) * op(B) + beta * C.
 //   ta == false: A stored M x K;  ta == true: A stored K x M, op(A) = A^T.
 //   B is stored K x N (no transpose needed by any caller).
-struct GemmOp {
+template <class Real>
+struct GemmOpT {
     int64_t M = 0, N = 0, K = 0;
-    const double *A = nullptr; int64_t lda = 1; bool ta = false; int maskA = MASK_NONE;
-    const double *B = nullptr; int64_t ldb = 1; int maskB = MASK_NONE;
-    double *C = nullptr; int64_t ldc = 1;
-    double alpha = 1.0, beta = 0.0;
+    const Real *A = nullptr; int64_t lda = 1; bool ta = false; int maskA = MASK_NONE;
+    const Real *B = nullptr; int64_t ldb = 1; int maskB = MASK_NONE;
+    Real *C = nullptr; int64_t ldc = 1;
+    Real alpha = Real(1), beta = Real(0);
 };
+using GemmOp = GemmOpT<double>;
 
 // Scratch for split-K: partial tiles and self-resetting per-tile counters
 // (must be zero before the first use; every launch leaves them zero).
-struct GemmScratch {
-    double *partial = nullptr; size_t partial_elems = 0;
+template <class Real>
+struct GemmScratchT {
+    Real *partial = nullptr; size_t partial_elems = 0;
     unsigned *counters = nullptr; size_t ncounters = 0;
 };
+using GemmScratch = GemmScratchT<double>;
 
 size_t gemm_partial_elems_max(int num_sms);
 size_t gemm_counters_max(int num_sms);
-gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc);
+// Real = double (FP64 path) or float (FP32 batched path)
+template <class Real>
+gbqr_status gemm(const Exec &ex, const GemmOpT<Real> &op, const GemmScratchT<Real> &sc);
 // Algorithmic flops of op (structural zeros of masked operands excluded).
-double gemm_algorithmic_flops(const GemmOp &op);
+template <class Real>
+double gemm_algorithmic_flops(const GemmOpT<Real> &op);
 
 #define TRY_ST(x) do { gbqr_status _s = (x); if (_s != GBQR_OK) return _s; } while (0)
 
@@ -112,25 +119,31 @@ struct TsqrPlan {
     size_t nR = 0, nT = 0, nY = 0, nX = 0, ncount = 0;
 };
 
-struct TsqrWork {
-    double *R = nullptr, *T = nullptr, *Y = nullptr, *X = nullptr;
+template <class Real>
+struct TsqrWorkT {
+    Real *R = nullptr, *T = nullptr, *Y = nullptr, *X = nullptr;
     unsigned *counters = nullptr;   // zero before first use; left zero
 };
+using TsqrWork = TsqrWorkT<double>;
 
 // Plan for an mp x w panel.  leaf_rows = target leaf height (0 = default),
 // fanout in [2, 8].  Returns false if the panel cannot be planned.
 bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPlan *plan);
 // Worst-case plan sizes over panels of height <= mp and width <= w.
 TsqrPlan tsqr_plan_bound(int64_t mp, int w, int leaf_rows, int fanout, int num_sms);
-gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &plan, double *A, int64_t lda,
-                     double *Tout, int64_t ldt, const TsqrWork &work);
+// Real = double (FP64 path) or float (FP32 batched path); the plan's shared
+// memory sizes are the FP64 ones (enough for either).
+template <class Real>
+gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &plan, Real *A, int64_t lda,
+                     Real *Tout, int64_t ldt, const TsqrWorkT<Real> &work);
 
 // ------------------------------------------------------------ small kernels
 gbqr_status fill_identity(const Exec &ex, int64_t m, int64_t n, double *Q, int64_t ldq);
 gbqr_status zero_strict_lower(const Exec &ex, int64_t n, double *T, int64_t ldt);
 gbqr_status copy_matrix(const Exec &ex, int64_t m, int64_t n, const double *src, int64_t lds,
                         double *dst, int64_t ldd);
-gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda,
+template <class Real>
+gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const Real *A, int64_t lda,
                            unsigned long long *flag);
 // x (n) <- R^{-1} x, R upper triangular n x n (ldr); records the first zero
 // diagonal index (or leaves *rankdef untouched) via atomicMin.
@@ -172,8 +185,9 @@ gbqr_status factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_
                            int t_layout, const gbqr_opts *opts);
 // prepare_only: validate, create the lane streams and size the workspace,
 // enqueue nothing (what a graph capture of the same call needs beforehand).
-gbqr_status factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, double *const *A,
-                                   const int64_t *lda, double *const *T, const int64_t *ldt, const gbqr_opts *opts,
+template <class Real>
+gbqr_status factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t *m, const int64_t *n, Real *const *A,
+                                   const int64_t *lda, Real *const *T, const int64_t *ldt, const gbqr_opts *opts,
                                    bool prepare_only = false);
 
 }  // namespace gbqr

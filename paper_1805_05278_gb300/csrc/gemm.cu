@@ -18,6 +18,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace gbqr {
 namespace {
@@ -25,30 +26,37 @@ namespace {
 constexpr int BK = 16;
 constexpr int kGroup = 8;   // fan-in of the split-K reduction tree
 
-struct GemmParams {
+template <class Real>
+struct GemmParamsT {
     int64_t M, N, K;
-    const double *A; int64_t lda; int maskA;
-    const double *B; int64_t ldb; int maskB;
-    double *C; int64_t ldc;
-    double alpha, beta;
-    double *partial;          // per tile: slots_per_tile * BM*BN doubles
+    const Real *A; int64_t lda; int maskA;
+    const Real *B; int64_t ldb; int maskB;
+    Real *C; int64_t ldc;
+    Real alpha, beta;
+    Real *partial;            // per tile: slots_per_tile * BM*BN elements
     unsigned *counters;       // per tile: counters_per_tile
     int slots_per_tile, counters_per_tile;
 };
+using GemmParams = GemmParamsT<double>;
 
-__device__ __forceinline__ double masked(const double *X, int64_t ld, int64_t r, int64_t c, int mask) {
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <class Real>
+__device__ __forceinline__ Real masked(const Real *X, int64_t ld, int64_t r, int64_t c, int mask) {
     if (mask == MASK_UNIT_LOWER) {
-        if (r < c) return 0.0;
-        if (r == c) return 1.0;
+        if (r < c) return Real(0);
+        if (r == c) return Real(1);
     } else if (mask == MASK_UPPER) {
-        if (r > c) return 0.0;
+        if (r > c) return Real(0);
     }
     return X[r + c * ld];
 }
 
 // K range [kb, ke) outside which op(A)(i, k) or op(B)(k, j) is structurally
 // zero for every i in [m0, m0+BM) and j in [n0, n0+BN).
-__device__ __forceinline__ void k_range(const GemmParams &p, bool ta, int64_t m0, int64_t n0,
+template <class P>
+__device__ __forceinline__ void k_range(const P &p, bool ta, int64_t m0, int64_t n0,
                                         int BM, int BN, int64_t &kb, int64_t &ke) {
     kb = 0; ke = p.K;
     if (p.maskA == MASK_UNIT_LOWER) {
@@ -62,11 +70,11 @@ __device__ __forceinline__ void k_range(const GemmParams &p, bool ta, int64_t m0
     else if (p.maskB == MASK_UPPER) ke = min(ke, n0 + BN);  // B(k,j) != 0 needs k <= j
 }
 
-template <int BM, int BN, bool TA>
-__global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
+template <class Real, int BM, int BN, bool TA>
+__global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParamsT<Real> p) {
     constexpr int RM = BM / 16, RN = BN / 16;
-    __shared__ double As[BK][BM + 1];
-    __shared__ double Bs[BK][BN + 1];
+    __shared__ Real As[BK][BM + 1];
+    __shared__ Real Bs[BK][BN + 1];
     __shared__ int s_last;
 
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -83,11 +91,11 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
         k_hi = min(ke, k_lo + chunk);
     }
 
-    double acc[RM][RN];
+    Real acc[RM][RN];
 #pragma unroll
     for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int c = 0; c < RN; ++c) acc[r][c] = 0.0;
+        for (int c = 0; c < RN; ++c) acc[r][c] = Real(0);
 
     for (int64_t k0 = k_lo; k0 < k_hi; k0 += BK) {
         // op(A) tile: rows m0.., k0..
@@ -97,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
             if (!TA) { i = idx % BM; kk = idx / BM; }   // coalesced along rows of stored A
             else     { kk = idx % BK; i = idx / BK; }   // coalesced along rows of stored A (= k)
             const int64_t gi = m0 + i, gk = k0 + kk;
-            double v = 0.0;
+            Real v = Real(0);
             if (gi < p.M && gk < k_hi) v = TA ? masked(p.A, p.lda, gk, gi, p.maskA)
                                               : masked(p.A, p.lda, gi, gk, p.maskA);
             As[kk][i] = v;
@@ -107,14 +115,14 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
         for (int idx = tid; idx < BK * BN; idx += kThreads) {
             const int kk = idx % BK, j = idx / BK;
             const int64_t gk = k0 + kk, gj = n0 + j;
-            double v = 0.0;
+            Real v = Real(0);
             if (gj < p.N && gk < k_hi) v = masked(p.B, p.ldb, gk, gj, p.maskB);
             Bs[kk][j] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[RM], b[RN];
+            Real a[RM], b[RN];
 #pragma unroll
             for (int r = 0; r < RM; ++r) a[r] = As[kk][tx + 16 * r];
 #pragma unroll
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
-                for (int c = 0; c < RN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+                for (int c = 0; c < RN; ++c) acc[r][c] = rfma(a[r], b[c], acc[r][c]);
         }
         __syncthreads();
     }
@@ -130,11 +138,11 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
     if (S > 1) {
         // Split-K: deterministic tree of last-arriver reductions.
         const int64_t tile = blockIdx.x + (int64_t)blockIdx.y * gridDim.x;
-        double *tp = p.partial + (size_t)tile * p.slots_per_tile * (BM * BN);
+        Real *tp = p.partial + (size_t)tile * p.slots_per_tile * (BM * BN);
         unsigned *tc = p.counters + (size_t)tile * p.counters_per_tile;
         int slot = z, Sl = S, base = 0, cbase = 0;
         for (;;) {
-            double *dst = tp + (size_t)(base + slot) * (BM * BN);
+            Real *dst = tp + (size_t)(base + slot) * (BM * BN);
 #pragma unroll
             for (int r = 0; r < RM; ++r)
 #pragma unroll
@@ -156,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
             for (int r = 0; r < RM; ++r)
 #pragma unroll
                 for (int c = 0; c < RN; ++c) {
-                    double s = 0.0;
+                    Real s = Real(0);
                     for (int q = 0; q < cnt; ++q)
                         s += __ldcg(tp + (size_t)(base + first + q) * (BM * BN) + (tx + 16 * r) + (ty + 16 * c) * BM);
                     acc[r][c] = s;
@@ -177,9 +185,9 @@ __global__ void __launch_bounds__(kThreads) dgemm_kernel(GemmParams p) {
         for (int r = 0; r < RM; ++r) {
             const int64_t gi = m0 + tx + 16 * r;
             if (gi >= p.M) continue;
-            double *cp = p.C + gi + gj * p.ldc;
-            double v = p.alpha * acc[r][c];
-            if (p.beta != 0.0) v = fma(p.beta, *cp, v);
+            Real *cp = p.C + gi + gj * p.ldc;
+            Real v = p.alpha * acc[r][c];
+            if (p.beta != Real(0)) v = rfma(p.beta, *cp, v);
             *cp = v;
         }
     }
@@ -340,19 +348,19 @@ void tree_shape(int S, int *slots, int *counters) {
     *counters = std::max(c, 1);
 }
 
-template <int BM, int BN>
-cudaError_t launch_bm_bn(const GemmParams &p, bool ta, dim3 grid, cudaStream_t st) {
-    if (ta) dgemm_kernel<BM, BN, true><<<grid, kThreads, 0, st>>>(p);
-    else dgemm_kernel<BM, BN, false><<<grid, kThreads, 0, st>>>(p);
+template <class Real, int BM, int BN>
+cudaError_t launch_bm_bn(const GemmParamsT<Real> &p, bool ta, dim3 grid, cudaStream_t st) {
+    if (ta) dgemm_kernel<Real, BM, BN, true><<<grid, kThreads, 0, st>>>(p);
+    else dgemm_kernel<Real, BM, BN, false><<<grid, kThreads, 0, st>>>(p);
     return cudaPeekAtLastError();
 }
 
-template <int BM>
-cudaError_t launch_bm(int BN, const GemmParams &p, bool ta, dim3 grid, cudaStream_t st) {
+template <class Real, int BM>
+cudaError_t launch_bm(int BN, const GemmParamsT<Real> &p, bool ta, dim3 grid, cudaStream_t st) {
     switch (BN) {
-        case 16: return launch_bm_bn<BM, 16>(p, ta, grid, st);
-        case 32: return launch_bm_bn<BM, 32>(p, ta, grid, st);
-        default: return launch_bm_bn<BM, 64>(p, ta, grid, st);
+        case 16: return launch_bm_bn<Real, BM, 16>(p, ta, grid, st);
+        case 32: return launch_bm_bn<Real, BM, 32>(p, ta, grid, st);
+        default: return launch_bm_bn<Real, BM, 64>(p, ta, grid, st);
     }
 }
 
@@ -369,7 +377,8 @@ size_t gemm_partial_elems_max(int num_sms) {
 
 size_t gemm_counters_max(int num_sms) { return (size_t)kMaxSplitCtasPerSm * num_sms * 2 + 64; }
 
-double gemm_algorithmic_flops(const GemmOp &op) {
+template <class Real>
+double gemm_algorithmic_flops(const GemmOpT<Real> &op) {
     // 2*M*N*K for a dense product; a masked triangular operand halves its
     // square part.  (Exact for the shapes used: the triangle is the leading
     // square of the masked operand.)
@@ -384,10 +393,11 @@ double gemm_algorithmic_flops(const GemmOp &op) {
     return f;
 }
 
-gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc) {
+template <class Real>
+gbqr_status gemm(const Exec &ex, const GemmOpT<Real> &op, const GemmScratchT<Real> &sc) {
     if (op.M <= 0 || op.N <= 0) return GBQR_OK;
     if (op.K <= 0) {
-        if (op.beta == 1.0) return GBQR_OK;
+        if (op.beta == Real(1)) return GBQR_OK;
     }
     const int BM = tile_for(op.M), BN = tile_for(op.N);
     const int64_t tm = (op.M + BM - 1) / BM, tn = (op.N + BN - 1) / BN;
@@ -411,7 +421,7 @@ gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc) {
             if (eff > best + 1e-9) { best = eff; S = (int)s; }
         }
     }
-    GemmParams p;
+    GemmParamsT<Real> p;
     p.M = op.M; p.N = op.N; p.K = std::max<int64_t>(op.K, 0);
     p.A = op.A; p.lda = op.lda; p.maskA = op.maskA;
     p.B = op.B; p.ldb = op.ldb; p.maskB = op.maskB;
@@ -427,20 +437,31 @@ gbqr_status gemm(const Exec &ex, const GemmOp &op, const GemmScratch &sc) {
     dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)S);
     trace_begin(ex, FAM_GEMM);
     cudaError_t e;
-    if (BM == 64 && BN == 64 && ex.dmma) {
-        if (op.ta) dgemm_dmma_kernel<true><<<grid, kThreads, 0, ex.stream>>>(p);
-        else dgemm_dmma_kernel<false><<<grid, kThreads, 0, ex.stream>>>(p);
-        e = cudaPeekAtLastError();
-    } else {
+    bool launched = false;
+    if constexpr (std::is_same<Real, double>::value) {
+        if (BM == 64 && BN == 64 && ex.dmma) {
+            if (op.ta) dgemm_dmma_kernel<true><<<grid, kThreads, 0, ex.stream>>>(p);
+            else dgemm_dmma_kernel<false><<<grid, kThreads, 0, ex.stream>>>(p);
+            e = cudaPeekAtLastError();
+            launched = true;
+        }
+    }
+    if (!launched) {
         switch (BM) {
-            case 16: e = launch_bm<16>(BN, p, op.ta, grid, ex.stream); break;
-            case 32: e = launch_bm<32>(BN, p, op.ta, grid, ex.stream); break;
-            default: e = launch_bm<64>(BN, p, op.ta, grid, ex.stream); break;
+            case 16: e = launch_bm<Real, 16>(BN, p, op.ta, grid, ex.stream); break;
+            case 32: e = launch_bm<Real, 32>(BN, p, op.ta, grid, ex.stream); break;
+            default: e = launch_bm<Real, 64>(BN, p, op.ta, grid, ex.stream); break;
         }
     }
     if (e != cudaSuccess) return GBQR_ECUDA;
-    const double bytes = 8.0 * ((double)op.M * op.K + (double)op.K * op.N + (op.beta != 0.0 ? 2.0 : 1.0) * op.M * op.N);
+    const double bytes = (double)sizeof(Real) *
+                         ((double)op.M * op.K + (double)op.K * op.N + (op.beta != Real(0) ? 2.0 : 1.0) * op.M * op.N);
     return trace_end(ex, FAM_GEMM, gemm_algorithmic_flops(op), bytes);
 }
+
+template gbqr_status gemm<double>(const Exec &, const GemmOpT<double> &, const GemmScratchT<double> &);
+template gbqr_status gemm<float>(const Exec &, const GemmOpT<float> &, const GemmScratchT<float> &);
+template double gemm_algorithmic_flops<double>(const GemmOpT<double> &);
+template double gemm_algorithmic_flops<float>(const GemmOpT<float> &);
 
 }  // namespace gbqr

@@ -31,18 +31,25 @@
 namespace gbqr {
 namespace {
 
-struct TsqrParams {
-    double *A; int64_t lda;     // panel top-left, mp x w
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double real_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float real_sqrt(float x) { return sqrtf(x); }
+
+template <class Real>
+struct TsqrParamsT {
+    Real *A; int64_t lda;     // panel top-left, mp x w
     int64_t mp; int w;
     int P, k, L, ldS, ldW;
-    double *wsR, *wsT, *wsY, *wsX;
+    Real *wsR, *wsT, *wsY, *wsX;
     unsigned *counters;
-    double *Tout; int64_t ldt;
+    Real *Tout; int64_t ldt;
 };
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class Real>
+__device__ __forceinline__ Real warp_sum(Real v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
@@ -51,17 +58,17 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Warp sums of N <= 4 per-lane values; every lane receives all N sums.  For
 // N > 1 a butterfly reduce-scatter (halve the set at offsets 16 and 8, then
 // three full stages) costs 6 FP64 adds instead of 5 per value.
-template <int N>
-__device__ __forceinline__ void warp_sum_n(double (&v)[4]) {
+template <int N, class Real>
+__device__ __forceinline__ void warp_sum_n(Real (&v)[4]) {
     if (N == 1) { v[0] = warp_sum(v[0]); return; }
     const int lane = threadIdx.x & 31;
     const bool h16 = lane & 16, h8 = lane & 8;
-    double k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
-    const double s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
+    Real k0 = h16 ? v[2] : v[0], k1 = h16 ? v[3] : v[1];
+    const Real s0 = h16 ? v[0] : v[2], s1 = h16 ? v[1] : v[3];
     k0 += __shfl_xor_sync(kFull, s0, 16);
     k1 += __shfl_xor_sync(kFull, s1, 16);
-    double k = h8 ? k1 : k0;
-    const double s = h8 ? k0 : k1;
+    Real k = h8 ? k1 : k0;
+    const Real s = h8 ? k0 : k1;
     k += __shfl_xor_sync(kFull, s, 8);
     k += __shfl_xor_sync(kFull, k, 4);
     k += __shfl_xor_sync(kFull, k, 2);
@@ -116,21 +123,21 @@ struct MergeRows {
 // gives v = e_c, tau = 2.  With d = alpha - beta (no cancellation) and
 // q = 1 / (beta d): scale = 1/d = beta q and tau = (beta - alpha)/beta = -d^2 q,
 // so the pivot costs one square root and one reciprocal.
-template <class Rows>
-__device__ void warp_pivot(double *S, int ldS, int c, const Rows &rows, double *tau) {
+template <class Real, class Rows>
+__device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau) {
     const int lane = threadIdx.x & 31;
-    double *col = S + (size_t)c * ldS;
-    double part = 0.0;
-    rows.each(c, lane, [&](int r) { const double x = col[r]; part = fma(x, x, part); });
-    const double sig2 = warp_sum(part);
-    const double alpha = col[c];
-    const double nrm = sqrt(fma(alpha, alpha, sig2));
-    const double beta = alpha < 0.0 ? nrm : -nrm;
-    double tj = 2.0;
-    if (beta != 0.0) {
-        const double d = alpha - beta;
-        const double q = 1.0 / (beta * d);
-        const double scal = beta * q;
+    Real *col = S + (size_t)c * ldS;
+    Real part = Real(0);
+    rows.each(c, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
+    const Real sig2 = warp_sum(part);
+    const Real alpha = col[c];
+    const Real nrm = real_sqrt(rfma(alpha, alpha, sig2));
+    const Real beta = alpha < Real(0) ? nrm : -nrm;
+    Real tj = Real(2);
+    if (beta != Real(0)) {
+        const Real d = alpha - beta;
+        const Real q = Real(1) / (beta * d);
+        const Real scal = beta * q;
         tj = -(d * d) * q;
         rows.each(c, lane, [&](int r) { col[r] *= scal; });
     }
@@ -142,26 +149,26 @@ __device__ void warp_pivot(double *S, int ldS, int c, const Rows &rows, double *
 // One warp applies reflector j to N columns (c > j: A(:,c) -= tau_j v_j (v_j^T A(:,c)))
 // or, for c < j, records the Gram entry G(c, j) = v_c^T v_j: both need the
 // same inner product s_c = A(j, c) + sum_r v_j(r) A(r, c).
-template <int N, class Rows>
-__device__ __forceinline__ void warp_apply(double *S, int ldS, int j, const Rows &rows, const int (&cols)[4],
-                                           double tj, double *G, int w) {
+template <int N, class Real, class Rows>
+__device__ __forceinline__ void warp_apply(Real *S, int ldS, int j, const Rows &rows, const int (&cols)[4],
+                                           Real tj, Real *G, int w) {
     const int lane = threadIdx.x & 31;
-    const double *vj = S + (size_t)j * ldS;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const Real *vj = S + (size_t)j * ldS;
+    Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
     rows.each_with_pivot(j, lane, [&](int r, bool piv) {
-        const double v = piv ? 1.0 : vj[r];
+        const Real v = piv ? Real(1) : vj[r];
 #pragma unroll
-        for (int q = 0; q < N; ++q) acc[q] = fma(v, S[r + (size_t)cols[q] * ldS], acc[q]);
+        for (int q = 0; q < N; ++q) acc[q] = rfma(v, S[r + (size_t)cols[q] * ldS], acc[q]);
     });
     warp_sum_n<N>(acc);
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         const int c = cols[q];
         if (c > j) {
-            const double f = tj * acc[q];
-            double *colc = S + (size_t)c * ldS;
+            const Real f = tj * acc[q];
+            Real *colc = S + (size_t)c * ldS;
             rows.each_with_pivot(j, lane, [&](int r, bool piv) {
-                colc[r] = fma(-f, piv ? 1.0 : vj[r], colc[r]);
+                colc[r] = rfma(-f, piv ? Real(1) : vj[r], colc[r]);
             });
         } else if (lane == 0) {
             G[c + j * w] = acc[q];
@@ -180,13 +187,13 @@ __device__ __forceinline__ void warp_apply(double *S, int ldS, int j, const Rows
 // reduction) carries nothing else.  On return: R on and above the pivots, the vectors below them
 // (unit pivot implied), tau[0:w], and the strict upper Gram matrix
 // G(c, j) = v_c^T v_j (ld w) from which the kernel T is built.
-template <class Rows>
-__device__ void householder_block(double *S, int ldS, int w, const Rows &rows, double *tau, double *G) {
+template <class Real, class Rows>
+__device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, Real *tau, Real *G) {
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (wid == 0) warp_pivot(S, ldS, 0, rows, tau);
     __syncthreads();
     for (int j = 0; j < w; ++j) {
-        const double tj = tau[j];
+        const Real tj = tau[j];
         const int nxt = j + 1;
         const int pw = j % nw;                         // pivot warp of this step
         if (wid == pw) {
@@ -221,11 +228,12 @@ __device__ void householder_block(double *S, int ldS, int w, const Rows &rows, d
 // pair of adjacent diagonal blocks T12 = -T11 G12 T22 (the T assembly of
 // Algorithm 2), so the dependency depth is log2(w) small products instead of
 // a w-step recurrence.  M is w x w scratch.  T, G, M: ld w, shared memory.
-__device__ void build_t(double *T, const double *G, const double *tau, double *M, int w) {
+template <class Real>
+__device__ void build_t(Real *T, const Real *G, const Real *tau, Real *M, int w) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int idx = tid; idx < w * w; idx += nthr) {
         const int i = idx % w, c = idx / w;
-        T[idx] = (i == c) ? tau[i] : 0.0;
+        T[idx] = (i == c) ? tau[i] : Real(0);
     }
     __syncthreads();
     for (int s = 1; s < w; s *= 2) {
@@ -234,8 +242,8 @@ __device__ void build_t(double *T, const double *G, const double *tau, double *M
             const int row = idx % w, col = idx / w;
             const int b1 = (row / s2) * s2 + s;
             if (row >= b1 || col < b1 || col >= b1 + s) continue;
-            double acc = 0.0;   // (G12 T22)(row, col)
-            for (int l = b1; l <= col; ++l) acc = fma(G[row + l * w], T[l + col * w], acc);
+            Real acc = Real(0);   // (G12 T22)(row, col)
+            for (int l = b1; l <= col; ++l) acc = rfma(G[row + l * w], T[l + col * w], acc);
             M[idx] = acc;
         }
         __syncthreads();
@@ -243,8 +251,8 @@ __device__ void build_t(double *T, const double *G, const double *tau, double *M
             const int row = idx % w, col = idx / w;
             const int b1 = (row / s2) * s2 + s;
             if (row >= b1 || col < b1 || col >= b1 + s) continue;
-            double acc = 0.0;   // (T11 M)(row, col)
-            for (int l = row; l < b1; ++l) acc = fma(T[row + l * w], M[l + col * w], acc);
+            Real acc = Real(0);   // (T11 M)(row, col)
+            for (int l = row; l < b1; ++l) acc = rfma(T[row + l * w], M[l + col * w], acc);
             T[idx] = -acc;
         }
         __syncthreads();
@@ -252,13 +260,15 @@ __device__ void build_t(double *T, const double *G, const double *tau, double *M
 }
 
 // Up kernel shared memory: S (ldS x w), then T, G (w x w each), tau (w).
-__global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
-    extern __shared__ double smem[];
+template <class Real>
+__global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *smem = reinterpret_cast<Real *>(smem_raw);
     const int w = p.w, ldS = p.ldS, tid = threadIdx.x, nthr = blockDim.x;
-    double *S = smem;
-    double *T = S + (size_t)ldS * w;
-    double *G = T + w * w;
-    double *tau = G + w * w;
+    Real *S = smem;
+    Real *T = S + (size_t)ldS * w;
+    Real *G = T + w * w;
+    Real *tau = G + w * w;
     __shared__ int s_last;
 
     const int leaf = blockIdx.x;
@@ -276,16 +286,16 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
     for (int c = 0; c < w; ++c)
         for (int r = tid; r < h; r += nthr) p.A[(r0 + r) + c * p.lda] = S[(size_t)c * ldS + r];
     {
-        double *Rn = p.wsR + (size_t)leaf * ww;
+        Real *Rn = p.wsR + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int i = idx % w, c = idx / w;
-            Rn[idx] = (i <= c) ? S[(size_t)c * ldS + i] : 0.0;
+            Rn[idx] = (i <= c) ? S[(size_t)c * ldS + i] : Real(0);
         }
     }
     __syncthreads();
     build_t(T, G, tau, S, w);
     {
-        double *Tn = p.wsT + (size_t)leaf * ww;
+        Real *Tn = p.wsT + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) Tn[idx] = T[idx];
     }
 
@@ -309,30 +319,30 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
             __threadfence();
             if (tid == 0) p.counters[pidx - p.P] = 0u;
             for (int i = 0; i < cnt; ++i) {
-                const double *Rc = p.wsR + (size_t)(off + first + i) * ww;
+                const Real *Rc = p.wsR + (size_t)(off + first + i) * ww;
                 for (int idx = tid; idx < w * w; idx += nthr)
                     S[(size_t)(idx / w) * ldS + i * w + (idx % w)] = __ldcg(Rc + idx);
             }
             __syncthreads();
             householder_block(S, ldS, w, MergeRows{w, cnt}, tau, G);
-            double *Rn = p.wsR + (size_t)pidx * ww, *Tn = p.wsT + (size_t)pidx * ww;
-            double *Yn = p.wsY + (size_t)(pidx - p.P) * (p.k - 1) * ww;
+            Real *Rn = p.wsR + (size_t)pidx * ww, *Tn = p.wsT + (size_t)pidx * ww;
+            Real *Yn = p.wsY + (size_t)(pidx - p.P) * (p.k - 1) * ww;
             for (int idx = tid; idx < w * w; idx += nthr) {
                 const int i = idx % w, c = idx / w;
-                Rn[idx] = (i <= c) ? S[(size_t)c * ldS + i] : 0.0;
+                Rn[idx] = (i <= c) ? S[(size_t)c * ldS + i] : Real(0);
             }
             for (int b = 1; b < cnt; ++b)
                 for (int idx = tid; idx < w * w; idx += nthr) {
                     const int i = idx % w, c = idx / w;
-                    Yn[(size_t)(b - 1) * ww + idx] = (i <= c) ? S[(size_t)c * ldS + b * w + i] : 0.0;
+                    Yn[(size_t)(b - 1) * ww + idx] = (i <= c) ? S[(size_t)c * ldS + b * w + i] : Real(0);
                 }
             __syncthreads();
             build_t(T, G, tau, S, w);
             for (int idx = tid; idx < w * w; idx += nthr) Tn[idx] = T[idx];
         } else {
             // single child: the node is the identity, its R passes through
-            const double *Rc = p.wsR + (size_t)(off + node) * ww;
-            double *Rn = p.wsR + (size_t)pidx * ww;
+            const Real *Rc = p.wsR + (size_t)(off + node) * ww;
+            Real *Rn = p.wsR + (size_t)pidx * ww;
             for (int idx = tid; idx < w * w; idx += nthr) Rn[idx] = Rc[idx];
         }
         node = parent;
@@ -344,11 +354,12 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParams p) {
 
 // C = sign * A * B for upper triangular w x w A, B (ld w): C is upper
 // triangular, its strict lower part is written as zero.
-__device__ void upper_upper(const double *A, const double *B, double *C, int w, double sign) {
+template <class Real>
+__device__ void upper_upper(const Real *A, const Real *B, Real *C, int w, Real sign) {
     for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
         const int i = idx % w, c = idx / w;
-        double s = 0.0;
-        for (int l = i; l <= c; ++l) s = fma(A[i + l * w], B[l + c * w], s);
+        Real s = Real(0);
+        for (int l = i; l <= c; ++l) s = rfma(A[i + l * w], B[l + c * w], s);
         C[idx] = sign * s;
     }
 }
@@ -357,14 +368,16 @@ __device__ void upper_upper(const double *A, const double *B, double *C, int w, 
 // its child [B_0; B_1; ...] = (I - V T V^T)[B; 0] = [B - T B; -Y_1 T B; ...].
 // T, Y and I are upper triangular, so every B stays upper triangular and each
 // product costs about w^3/6 multiply-adds.
-__global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
-    extern __shared__ double smem[];
+template <class Real>
+__global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *smem = reinterpret_cast<Real *>(smem_raw);
     const int w = p.w, ldS = p.ldW, tid = threadIdx.x, nthr = blockDim.x;
     const size_t ww = (size_t)w * w;
-    double *B = smem;
-    double *C = B + ww;
-    double *M = C + ww;      // node T / Y, then leaf T_p and products
-    double *Vs = M + ww;     // leaf block, ldS x w
+    Real *B = smem;
+    Real *C = B + ww;
+    Real *M = C + ww;      // node T / Y, then leaf T_p and products
+    Real *Vs = M + ww;     // leaf block, ldS x w
 
     const int leaf = blockIdx.x;
     const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
@@ -378,7 +391,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
         Nlev[lv + 1] = (Nlev[lv] + p.k - 1) / p.k;
         offl[lv + 1] = offl[lv] + Nlev[lv];
     }
-    for (int idx = tid; idx < w * w; idx += nthr) B[idx] = (idx % w == idx / w) ? 1.0 : 0.0;
+    for (int idx = tid; idx < w * w; idx += nthr) B[idx] = (idx % w == idx / w) ? Real(1) : Real(0);
     __syncthreads();
     for (int lv = p.L - 1; lv >= 0; --lv) {
         const int parent = anc[lv + 1], first = parent * p.k;
@@ -386,18 +399,18 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
         if (cnt == 1) continue;
         const int pos = anc[lv] - first;
         const int64_t pidx = offl[lv + 1] + parent;
-        const double *Tn = p.wsT + (size_t)pidx * ww;
+        const Real *Tn = p.wsT + (size_t)pidx * ww;
         for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tn[idx];
         __syncthreads();
-        upper_upper(M, B, C, w, 1.0);          // C = T_node B
+        upper_upper(M, B, C, w, Real(1));          // C = T_node B
         __syncthreads();
         if (pos == 0) {
             for (int idx = tid; idx < w * w; idx += nthr) B[idx] -= C[idx];
         } else {
-            const double *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos - 1)) * ww;
+            const Real *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos - 1)) * ww;
             for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Yn[idx];
             __syncthreads();
-            upper_upper(M, C, B, w, -1.0);     // B = -Y_pos C
+            upper_upper(M, C, B, w, -Real(1));     // B = -Y_pos C
         }
         __syncthreads();
     }
@@ -406,29 +419,29 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
     for (int c = 0; c < w; ++c)
         for (int r = tid; r < h; r += nthr) Vs[(size_t)c * ldS + r] = p.A[(r0 + r) + c * p.lda];
     {
-        const double *Tp = p.wsT + (size_t)leaf * ww;
+        const Real *Tp = p.wsT + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tp[idx];
     }
     __syncthreads();
     // C = V1^T B, V1 = unit lower top w x w of the leaf block; B upper -> C upper
     for (int idx = tid; idx < w * w; idx += nthr) {
         const int i = idx % w, c = idx / w;
-        double s = 0.0;
+        Real s = Real(0);
         if (i <= c) {
             s = B[i + c * w];
-            for (int l = i + 1; l <= c; ++l) s = fma(Vs[(size_t)i * ldS + l], B[l + c * w], s);
+            for (int l = i + 1; l <= c; ++l) s = rfma(Vs[(size_t)i * ldS + l], B[l + c * w], s);
         }
         C[idx] = s;
     }
     __syncthreads();
     {
         // Z = T_p C into registers, then over M after a barrier
-        double z2[(kMaxPanel * kMaxPanel + kThreads - 1) / kThreads];
+        Real z2[(kMaxPanel * kMaxPanel + kThreads - 1) / kThreads];
         int q = 0;
         for (int idx = tid; idx < w * w; idx += nthr, ++q) {
             const int i = idx % w, c = idx / w;
-            double s = 0.0;
-            for (int l = i; l <= c; ++l) s = fma(M[i + l * w], C[l + c * w], s);
+            Real s = Real(0);
+            for (int l = i; l <= c; ++l) s = rfma(M[i + l * w], C[l + c * w], s);
             z2[q] = s;
         }
         __syncthreads();
@@ -440,10 +453,10 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
     for (int idx = tid; idx < h * w; idx += nthr) {
         const int r = idx % h, c = idx / h;
         const int iend = min(r, c + 1);
-        double s = 0.0;
-        for (int i = 0; i < iend; ++i) s = fma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
+        Real s = Real(0);
+        for (int i = 0; i < iend; ++i) s = rfma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
         if (r <= c) s += M[r + c * w];
-        const double wv = ((r < w) ? B[r + c * w] : 0.0) - s;
+        const Real wv = ((r < w) ? B[r + c * w] : Real(0)) - s;
         p.A[(r0 + r) + c * p.lda] = wv;
         if (leaf == 0 && r < w) p.wsX[r + c * w] = wv;
     }
@@ -451,11 +464,12 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParams p) {
 
 // Inverse of the unit lower triangular L (ld w) into Li (ld w), blocked
 // bottom-up like build_t: Li21 = -Li22 L21 Li11 for each pair of blocks.
-__device__ void unit_lower_inverse(const double *L, double *Li, double *M, int w) {
+template <class Real>
+__device__ void unit_lower_inverse(const Real *L, Real *Li, Real *M, int w) {
     const int tid = threadIdx.x, nthr = blockDim.x;
     for (int idx = tid; idx < w * w; idx += nthr) {
         const int i = idx % w, c = idx / w;
-        Li[idx] = (i == c) ? 1.0 : 0.0;
+        Li[idx] = (i == c) ? Real(1) : Real(0);
     }
     __syncthreads();
     for (int s = 1; s < w; s *= 2) {
@@ -464,8 +478,8 @@ __device__ void unit_lower_inverse(const double *L, double *Li, double *M, int w
             const int row = idx % w, col = idx / w;
             const int b1 = (col / s2) * s2 + s;   // pair (b0 = b1 - s, b1), col in block 0, row in block 1
             if (col >= b1 || row < b1 || row >= b1 + s) continue;
-            double acc = 0.0;   // (L21 Li11)(row, col)
-            for (int l = col; l < b1; ++l) acc = fma(L[row + l * w], Li[l + col * w], acc);
+            Real acc = Real(0);   // (L21 Li11)(row, col)
+            for (int l = col; l < b1; ++l) acc = rfma(L[row + l * w], Li[l + col * w], acc);
             M[idx] = acc;
         }
         __syncthreads();
@@ -473,47 +487,49 @@ __device__ void unit_lower_inverse(const double *L, double *Li, double *M, int w
             const int row = idx % w, col = idx / w;
             const int b1 = (col / s2) * s2 + s;
             if (col >= b1 || row < b1 || row >= b1 + s) continue;
-            double acc = M[idx];   // Li22(row,row) = 1
-            for (int l = b1; l < row; ++l) acc = fma(Li[row + l * w], M[l + col * w], acc);
+            Real acc = M[idx];   // Li22(row,row) = 1
+            for (int l = b1; l < row; ++l) acc = rfma(Li[row + l * w], M[l + col * w], acc);
             Li[idx] = -acc;
         }
         __syncthreads();
     }
 }
 
-__global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
-    extern __shared__ double smem[];
+template <class Real>
+__global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParamsT<Real> p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *smem = reinterpret_cast<Real *>(smem_raw);
     const int w = p.w, ldS = p.ldW, tid = threadIdx.x, nthr = blockDim.x;
     const size_t ww = (size_t)w * w;
-    double *X = smem;            // w x w: L (strict lower) and U (upper)
-    double *Tm = X + ww;         // w x w
-    double *Li = Tm + ww;        // w x w
-    double *Ms = Li + ww;        // w x w scratch
-    double *Sg = Ms + ww;        // w signs
-    double *rU = Sg + w;         // w reciprocals of diag(U)
-    double *Wb = rU + w;         // ldS x w
+    Real *X = smem;            // w x w: L (strict lower) and U (upper)
+    Real *Tm = X + ww;         // w x w
+    Real *Li = Tm + ww;        // w x w
+    Real *Ms = Li + ww;        // w x w scratch
+    Real *Sg = Ms + ww;        // w signs
+    Real *rU = Sg + w;         // w reciprocals of diag(U)
+    Real *Wb = rU + w;         // ldS x w
 
     for (int idx = tid; idx < w * w; idx += nthr) X[idx] = __ldcg(p.wsX + idx);
     __syncthreads();
     // X + S = L U, S_jj = sgn(X^_jj) added before column j is eliminated.
     for (int j = 0; j < w; ++j) {
         if (tid == 0) {
-            const double s = X[j + j * w] < 0.0 ? -1.0 : 1.0;
+            const Real s = X[j + j * w] < Real(0) ? -Real(1) : Real(1);
             Sg[j] = s;
             X[j + j * w] += s;
         }
         __syncthreads();
-        const double piv = X[j + j * w];
+        const Real piv = X[j + j * w];
         for (int i = j + 1 + tid; i < w; i += nthr) X[i + j * w] /= piv;
         __syncthreads();
         const int rem = w - j - 1;
         for (int idx = tid; idx < rem * rem; idx += nthr) {
             const int i = j + 1 + idx % rem, c = j + 1 + idx / rem;
-            X[i + c * w] = fma(-X[i + j * w], X[j + c * w], X[i + c * w]);
+            X[i + c * w] = rfma(-X[i + j * w], X[j + c * w], X[i + c * w]);
         }
         __syncthreads();
     }
-    for (int j = tid; j < w; j += nthr) rU[j] = 1.0 / X[j + j * w];
+    for (int j = tid; j < w; j += nthr) rU[j] = Real(1) / X[j + j * w];
 
     const int leaf = blockIdx.x;
     if (leaf == 0) {
@@ -521,8 +537,8 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
         unit_lower_inverse(X, Li, Ms, w);
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int i = idx % w, c = idx / w;
-            double t = 0.0;
-            for (int l = i; l <= c; ++l) t = fma(X[i + l * w] * Sg[l], (l == c) ? 1.0 : Li[c + l * w], t);
+            Real t = Real(0);
+            for (int l = i; l <= c; ++l) t = rfma(X[i + l * w] * Sg[l], (l == c) ? Real(1) : Li[c + l * w], t);
             Tm[idx] = t;
         }
         __syncthreads();
@@ -534,7 +550,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
         // on and above it; R^(L) sits in the last node slot (the root).
         int64_t nodes = p.P, Nl = p.P;
         while (Nl > 1) { Nl = (Nl + p.k - 1) / p.k; nodes += Nl; }
-        const double *RL = p.wsR + (size_t)(nodes - 1) * ww;
+        const Real *RL = p.wsR + (size_t)(nodes - 1) * ww;
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int i = idx % w, c = idx / w;
             p.A[i + c * p.lda] = (i <= c) ? -Sg[i] * __ldcg(RL + idx) : X[i + c * w];
@@ -551,8 +567,8 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParams p) {
     __syncthreads();
     for (int r = tid; r < h; r += nthr) {
         for (int j = 0; j < w; ++j) {
-            double v = Wb[(size_t)j * ldS + r];
-            for (int l = 0; l < j; ++l) v = fma(-Wb[(size_t)l * ldS + r], X[l + j * w], v);
+            Real v = Wb[(size_t)j * ldS + r];
+            for (int l = 0; l < j; ++l) v = rfma(-Wb[(size_t)l * ldS + r], X[l + j * w], v);
             Wb[(size_t)j * ldS + r] = v * rU[j];
         }
     }
@@ -646,9 +662,10 @@ TsqrPlan tsqr_plan_bound(int64_t mp, int w, int leaf_rows, int fanout, int num_s
     return best;
 }
 
-gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, double *A, int64_t lda,
-                     double *Tout, int64_t ldt, const TsqrWork &work) {
-    TsqrParams p;
+template <class Real>
+gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, Real *A, int64_t lda,
+                     Real *Tout, int64_t ldt, const TsqrWorkT<Real> &work) {
+    TsqrParamsT<Real> p;
     p.A = A; p.lda = lda; p.mp = pl.mp; p.w = pl.w;
     p.P = pl.P; p.k = pl.k; p.L = pl.L; p.ldS = pl.ldS; p.ldW = pl.ldW;
     p.wsR = work.R; p.wsT = work.T; p.wsY = work.Y; p.wsX = work.X;
@@ -658,9 +675,9 @@ gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, double *A, int64_t lda,
     static bool attr_done[64] = {false};
     if (ex.device >= 0 && ex.device < 64 && !attr_done[ex.device]) {
         const int cap = (int)kSmemCap;
-        if (cudaFuncSetAttribute(tsqr_up_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
-            cudaFuncSetAttribute(tsqr_down_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
-            cudaFuncSetAttribute(tsqr_recon_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
+        if (cudaFuncSetAttribute(tsqr_up_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
+            cudaFuncSetAttribute(tsqr_down_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
+            cudaFuncSetAttribute(tsqr_recon_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
             return GBQR_ECUDA;
         attr_done[ex.device] = true;
     }
@@ -669,23 +686,28 @@ gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, double *A, int64_t lda,
     gbqr_status st;
 
     trace_begin(ex, FAM_TSQR_UP);
-    tsqr_up_kernel<<<pl.P, kThreads, pl.smem_up, ex.stream>>>(p);
+    tsqr_up_kernel<Real><<<pl.P, kThreads, pl.smem_up, ex.stream>>>(p);
     // leaf Householder ~2 m w^2 + T ~ m w^2; merges ~ (nodes) * w^3
     st = trace_end(ex, FAM_TSQR_UP, 3.0 * mp * ww + (double)(pl.nodes - pl.P) * 1.5 * ww * w,
-                   8.0 * (2.0 * mp * w + 3.0 * (double)pl.nodes * ww));
+                   (double)sizeof(Real) * (2.0 * mp * w + 3.0 * (double)pl.nodes * ww));
     if (st != GBQR_OK) return st;
 
     trace_begin(ex, FAM_TSQR_DOWN);
-    tsqr_down_kernel<<<pl.P, kThreads, pl.smem_down, ex.stream>>>(p);
+    tsqr_down_kernel<Real><<<pl.P, kThreads, pl.smem_down, ex.stream>>>(p);
     st = trace_end(ex, FAM_TSQR_DOWN, 2.0 * mp * ww + (double)pl.P * (2.0 * pl.L + 2.0) * ww * w,
-                   8.0 * (2.0 * mp * w + 2.0 * (double)pl.nodes * ww));
+                   (double)sizeof(Real) * (2.0 * mp * w + 2.0 * (double)pl.nodes * ww));
     if (st != GBQR_OK) return st;
 
     trace_begin(ex, FAM_TSQR_RECON);
-    tsqr_recon_kernel<<<pl.P, kThreads, pl.smem_recon, ex.stream>>>(p);
+    tsqr_recon_kernel<Real><<<pl.P, kThreads, pl.smem_recon, ex.stream>>>(p);
     st = trace_end(ex, FAM_TSQR_RECON, mp * ww + (double)pl.P * ww * w * 2.0 / 3.0,
-                   8.0 * (2.0 * mp * w + 2.0 * ww));
+                   (double)sizeof(Real) * (2.0 * mp * w + 2.0 * ww));
     return st;
 }
+
+template gbqr_status tsqr_run<double>(const Exec &, const TsqrPlan &, double *, int64_t, double *, int64_t,
+                                     const TsqrWorkT<double> &);
+template gbqr_status tsqr_run<float>(const Exec &, const TsqrPlan &, float *, int64_t, float *, int64_t,
+                                    const TsqrWorkT<float> &);
 
 }  // namespace gbqr
