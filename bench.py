@@ -82,6 +82,7 @@ def parse():
     p.add_argument("--batched-steps", type=int, default=3)
     p.add_argument("--batched-streams", type=int, default=0)
     p.add_argument("--batched-cutoff", type=int, default=0)
+    p.add_argument("--batched-cutoff32", type=int, default=0, help="cutoff b of the FP32 batch (0: default 16)")
     p.add_argument("--serving", type=int, default=200, help="requests per serving run (0: skip)")
     p.add_argument("--serving-rates", default="100,400,1600,5000")
     p.add_argument("--serving-workers", type=int, default=16)
@@ -148,11 +149,33 @@ def measure_serving(gb, dev, args):
     return out
 
 
+def _time_batch_graph(gb, ctx, stream, buf, pristine, As, Ts, o, steps):
+    """Capture gbqr_factor_batched(As, Ts) into one graph; time `steps`
+    replays (inputs restored by one device copy before each, untimed)."""
+    import torch
+    with torch.cuda.stream(stream):
+        ctx.factor_batched(As, Ts, o)                   # warm-up: lanes, workspace
+        torch.cuda.synchronize()
+        graph = ctx.capture(lambda: ctx.factor_batched(As, Ts, o))
+        times = []
+        for _ in range(max(1, steps)):
+            buf.copy_(pristine)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.launch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    graph.close()
+    return sorted(times)[len(times) // 2]
+
+
 def measure_batched(gb, dev, args):
-    """The batched tall-skinny workload: args.batched FP64 matrices, m
-    log-uniform in [256, 16384], n uniform in [16, 256], factored by one
-    captured graph launch of gbqr_factor_batched.  Each timed step restores
-    the inputs with one device copy, then launches the graph."""
+    """The batched tall-skinny workload: args.batched matrices, m log-uniform
+    in [256, 16384], n uniform in [16, 256], factored by one captured graph
+    launch of gbqr_factor_batched (FP64), then the same matrices rounded to
+    FP32 by gbqr_factor_batched_f32.  Each timed step restores the inputs with
+    one device copy, then launches the graph."""
     import torch
     shapes = workloads.batched_shapes(args.batched, workloads.BATCHED_SEED)
     buf, offs = workloads.batched_device_buffer(shapes, workloads.BATCHED_SEED, f"cuda:{dev}")
@@ -168,29 +191,29 @@ def measure_batched(gb, dev, args):
         with torch.cuda.stream(stream):
             o, tune_ms = ctx.autotune_batched(shapes, gb.GBQR_FP64, args.batched_autotune_ms)
         tuned = gb.opts_dict(o)
-    with torch.cuda.stream(stream):
-        ctx.factor_batched(As, Ts, o)                   # warm-up: lanes, workspace
-        torch.cuda.synchronize()
-        graph = ctx.capture(lambda: ctx.factor_batched(As, Ts, o))
-        launches0 = ctx.launch_count()
-        times = []
-        for _ in range(max(1, args.batched_steps)):
-            buf.copy_(pristine)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            graph.launch()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            times.append(e0.elapsed_time(e1))
+    ms = _time_batch_graph(gb, ctx, stream, buf, pristine, As, Ts, o, args.batched_steps)
     st, _ = ctx.sync()
-    graph.close()
+    out = {"workload": f"{len(shapes)} matrices, m log-uniform [256, 16384], n uniform [16, 256], "
+                       f"iid N(0,1), seed {workloads.BATCHED_SEED}",
+           "total_flops": flops, "ms_per_batch": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+           "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st),
+           "streams": o.batch_streams or 128, "cutoff_b": o.cutoff_b or 16,
+           "tuned": tuned, "tuned_ms": tune_ms, "dtype": "f64"}
+    del As, Ts, buf, pristine
+    # FP32: the same matrices rounded to float32, FP32 arithmetic throughout
+    buf32, _ = workloads.batched_device_buffer(shapes, workloads.BATCHED_SEED, f"cuda:{dev}")
+    buf32 = buf32.float()
+    pristine32 = buf32.clone()
+    As32 = [buf32[o_:o_ + m * n].view(n, m).T for (m, n), o_ in zip(shapes, offs)]
+    Ts32 = [torch.empty((n, min(128, n)), dtype=torch.float32, device=f"cuda:{dev}").T for (m, n) in shapes]
+    o32 = gb.opts(cutoff_b=args.batched_cutoff32, batch_streams=args.batched_streams)
+    ms32 = _time_batch_graph(gb, ctx, stream, buf32, pristine32, As32, Ts32, o32, args.batched_steps)
+    st32, _ = ctx.sync()
+    out["fp32"] = {"ms_per_batch": ms32, "tflops": flops / (ms32 * 1e-3) / 1e12,
+                   "matrices_per_s": len(shapes) / (ms32 * 1e-3), "status": int(st32), "dtype": "f32",
+                   "cutoff_b": args.batched_cutoff32 or 16, "streams": args.batched_streams or 128}
     ctx.close()
-    ms = sorted(times)[len(times) // 2]
-    return {"workload": f"{len(shapes)} FP64 matrices, m log-uniform [256, 16384], n uniform [16, 256], seed {workloads.BATCHED_SEED}",
-            "total_flops": flops, "ms_per_batch": ms, "tflops": flops / (ms * 1e-3) / 1e12,
-            "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st),
-            "streams": o.batch_streams or 128, "cutoff_b": o.cutoff_b or 16,
-            "tuned": tuned, "tuned_ms": tune_ms}
+    return out
 
 
 def kappa_estimate(R, iters: int = 40) -> float:
