@@ -462,6 +462,14 @@ GBQR_API gbqr_status gbqr_tsqr_static(int64_t m, int64_t n, double *A, int64_t l
  * bytes.  Errors: EINVAL, ENOMEM, ECUDA. */
 GBQR_API gbqr_status gbqr_fp64_peak(int device, int kind, int iters, double *tflops);
 
+/* Failure-detection self-test: one CTA runs the bounded mbarrier wait of the
+ * tensor-core GEMM (about 2 s by %globaltimer) on a barrier that nothing
+ * arrives at.  Expected result: GBQR_ETIMEOUT with *completed = 0, and the
+ * device still usable afterwards (the kernel returns instead of hanging).
+ * The paper has no counterpart.  Synchronous (about 2 s); allocates 8 bytes.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_selftest_wait_timeout(int device, int *completed);
+
 /* Cycles per dependent FP64 operation of a warp when `warps` warps (1..32)
  * of one CTA run such chains at once: op 0 = FMA, 1 = sqrt, 2 = reciprocal
  * (each with an add).  The paper has no counterpart: it measures the issue

@@ -89,6 +89,19 @@ __device__ bool mbar_wait(uint32_t a, uint32_t parity, int *err) {
     }
 }
 
+// The bounded wait above on a barrier nothing ever arrives at: it must give
+// up after its time limit, raise the error flag and let the kernel return.
+__global__ void wait_selftest_kernel(int *err, int *completed) {
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t a = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(a, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *completed = mbar_wait(a, 0u, err) ? 1 : 0;
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int x, int y, int z, uint32_t mbar) {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -458,3 +471,24 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
 }
 
 }  // namespace gbqr
+
+extern "C" GBQR_API gbqr_status gbqr_selftest_wait_timeout(int device, int *completed) {
+    if (!completed) return GBQR_EINVAL;
+    *completed = -1;
+    if (cudaSetDevice(device) != cudaSuccess) return GBQR_ECUDA;
+    int *d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return GBQR_ENOMEM; }
+    int h[2] = {0, 0};
+    gbqr_status st = GBQR_OK;
+    if (cudaMemset(d, 0, 2 * sizeof(int)) != cudaSuccess) st = GBQR_ECUDA;
+    if (st == GBQR_OK) {
+        gbqr::wait_selftest_kernel<<<1, 32>>>(d, d + 1);
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = GBQR_ECUDA;
+    }
+    cudaFree(d);
+    if (st != GBQR_OK) return st;
+    *completed = h[1];
+    return h[0] ? GBQR_ETIMEOUT : GBQR_OK;
+}
