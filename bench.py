@@ -78,6 +78,9 @@ def parse():
     p.add_argument("--ls-decades", default="2,6,10", help="column-grading decades (kappa ~ 10^d x kappa(Gaussian))")
     p.add_argument("--ls-shapes", default="32768x2048,8192x8192")
     p.add_argument("--no-ls-kappa", action="store_true", help="skip the condition estimate (torch.linalg)")
+    p.add_argument("--ls-autotune-ms", type=float, default=0.0,
+                   help="gbqr_autotune budget per LS shape and precision before timing (0: defaults; the "
+                        "tuner's objective is the factorization, and it measured slower for the solve)")
     p.add_argument("--batched", type=int, default=2000, help="matrices in the batched measurement (0: skip)")
     p.add_argument("--batched-steps", type=int, default=3)
     p.add_argument("--batched-streams", type=int, default=0)
@@ -268,6 +271,11 @@ def measure_ls(gb, ctx, dev, args):
             row = {"m": m, "n": n, "decades": d, "kappa_est": kappa, "seed": seed}
             xs = {}
             for prec, name in [(gb.GBQR_FP64, "fp64"), (gb.GBQR_MIXED_SPLITBF16, "mixed_splitbf16")]:
+                # the tuner's choice for this shape class and precision (cached in ctx,
+                # picked up by gbqr_ls_solve); once per shape
+                if args.ls_autotune_ms > 0 and ctx.tuned(gb.GBQR_TUNE_FACTOR, m, n, gb.GBQR_T_PANEL, prec) is None:
+                    best, _ = ctx.autotune(m, n, gb.GBQR_T_PANEL, prec, args.ls_autotune_ms)
+                    row.setdefault("tuned", {})[name] = gb.opts_dict(best)
                 x = torch.zeros(n, dtype=torch.float64, device=devs)
                 st, info = ctx.ls_solve(A, b, x, prec)          # warm-up
                 times = []

@@ -330,8 +330,10 @@ GBQR_API gbqr_status gbqr_gemm_split_bf16(gbqr_ctx *ctx, int transa, int64_t M, 
  * *best_ms (may be NULL), and cached in the context for the power-of-two
  * class of (m, n), t_layout and update_prec.  Later calls of gbqr_factor and
  * gbqr_ls_solve on this context take the cached values for every option
- * field the caller leaves zero — except panel_nb in gbqr_factor, which fixes
- * the caller's T layout (pass best->panel_nb explicitly, with ldt >= it).
+ * field the caller leaves zero — except panel_nb: in gbqr_factor it fixes
+ * the caller's T layout (pass best->panel_nb explicitly, with ldt >= it), and
+ * gbqr_ls_solve keeps its default (the tuner times the factorization; the
+ * solve's refinement applies Q panel by panel).
  * Synchronous; allocates m*n + 256*n doubles for the duration.
  * Errors: EINVAL (m < n, n < 1, bad layout/precision, FULL with mixed),
  * ENOMEM, ECUDA. */
