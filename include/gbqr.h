@@ -193,6 +193,15 @@ GBQR_API gbqr_status gbqr_sync(gbqr_ctx *ctx, gbqr_info *info);
 GBQR_API gbqr_status gbqr_factor(gbqr_ctx *ctx, int64_t m, int64_t n, double *A, int64_t lda,
                         double *T, int64_t ldt, int t_layout, const gbqr_opts *opts);
 
+/* gbqr_factor in FP32: A (m x n, m >= n) and T are float DEVICE arrays and
+ * every step computes in FP32 with the float instantiations of the same
+ * kernels (TSQR, tiled GEMM); same layouts, options and look-ahead.
+ * opts->update_prec must be GBQR_FP64 / 0 (no tensor-core updates); the
+ * autotuner's cache is not used.  Errors: EINVAL (m < n, lda, ldt, opts),
+ * EUNSUPPORTED (host pointers), ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_factor_f32(gbqr_ctx *ctx, int64_t m, int64_t n, float *A, int64_t lda,
+                                     float *T, int64_t ldt, int t_layout, const gbqr_opts *opts);
+
 /* Default top-level panel width for GBQR_T_PANEL on an m x n problem. */
 GBQR_API int64_t gbqr_default_panel_nb(int64_t m, int64_t n);
 

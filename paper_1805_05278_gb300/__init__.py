@@ -77,6 +77,7 @@ SIGNATURES = {
     "gbqr_sync": (ctypes.c_int, [_P, ctypes.POINTER(gbqr_info)]),
     "gbqr_factor": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.POINTER(gbqr_opts)]),
     "gbqr_default_panel_nb": (_I64, [_I64, _I64]),
+    "gbqr_factor_f32": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, ctypes.POINTER(gbqr_opts)]),
     "gbqr_apply_qt": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _I64, _P, _I64]),
     "gbqr_apply_q": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _I64, _P, _I64]),
     "gbqr_form_q": (ctypes.c_int, [_P, _I64, _I64, _P, _I64, _P, _I64, ctypes.c_int, _I64, _P, _I64]),
@@ -279,11 +280,16 @@ class Context:
 
     # ---- computation
     def factor(self, A, T, layout: int = GBQR_T_PANEL, o: gbqr_opts | None = None) -> int:
-        """In-place QR of A (column-major m x n); T receives the kernel."""
-        pa, m, n, lda = _cm(A, "A")
-        pt, _, _, ldt = _cm(T, "T")
-        return check(gbqr_factor(self.handle, m, n, _P(pa), lda, _P(pt), ldt, layout,  # noqa: F821
-                                 ctypes.byref(o) if o is not None else None), "gbqr_factor")
+        """In-place QR of A (column-major m x n); T receives the kernel.
+        float32 tensors go to gbqr_factor_f32 (FP32 throughout)."""
+        import torch
+        dt = A.dtype if A.dtype == torch.float32 else torch.float64
+        pa, m, n, lda = _cm(A, "A", dt)
+        pt, _, _, ldt = _cm(T, "T", dt)
+        fn, nm = ((gbqr_factor_f32, "gbqr_factor_f32") if dt == torch.float32  # noqa: F821
+                  else (gbqr_factor, "gbqr_factor"))  # noqa: F821
+        return check(fn(self.handle, m, n, _P(pa), lda, _P(pt), ldt, layout,
+                        ctypes.byref(o) if o is not None else None), nm)
 
     def _apply(self, fn, VR, T, layout, nb, B):
         pv, m, n, lda = _cm(VR, "VR")

@@ -29,6 +29,8 @@ constexpr int64_t kDefaultPanel = 128;
 constexpr int kBatchLanes = 128;      // streams a batched factorization spreads over (measured best of 16..128)
 constexpr int kBatchCutoff = 16;      // batched default cutoff b (measured best of 16, 32)
 constexpr int kKrylov = 100;          // GMRES refinement: Arnoldi steps per correction
+constexpr int kInPanelTcMinCols = 32;  // mixed path: in-panel updates on the tensor cores from n1 >= 32 (16 measured slower) ...
+constexpr int64_t kInPanelTcMinRows = 2048;   // ... and m >= 2048
 constexpr int kMaxBatchLanes = 128;
 
 struct DeviceInfo {
@@ -114,6 +116,7 @@ struct Layout {
     size_t M1 = 0, M2 = 0, bigA = 0, bigT = 0, vec = 0;
     size_t partial2 = 0, gcount2 = 0, M1b = 0, M2b = 0;   // second lane (look-ahead panel stream)
     size_t tc = 0, n_tc = 0;                              // tensor-core slices (mixed updates)
+    size_t tc2 = 0, n_tc2 = 0;                            // ... of the look-ahead lane's in-panel updates
     size_t kry = 0, n_kry = 0;                            // least squares, mixed: Krylov basis of the refinement
     size_t total = 0;
     size_t n_partial = 0, n_gcount = 0, n_M = 0, n_Mb = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
@@ -159,6 +162,10 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
         L.n_tc = std::max(tc_gemm_scratch_bytes(nb, std::max<int64_t>(n, 1), std::max<int64_t>(m, 1), num_sms),
                           tc_gemm_scratch_bytes(std::max<int64_t>(m, 1), std::max<int64_t>(n, 1), nb, num_sms));
         L.tc = take(L.n_tc);
+        // in-panel updates (M, N <= nb/2, K <= m) on the look-ahead lane
+        const int64_t h = std::max<int64_t>(nb / 2, 1);
+        L.n_tc2 = pr.lookahead ? tc_gemm_scratch_bytes(h, h, std::max<int64_t>(m, 1), num_sms) : 0;
+        if (L.n_tc2) L.tc2 = take(L.n_tc2);
     }
     L.bigA = take(L.n_bigA * 8);
     L.bigT = take(L.n_bigT * 8);
@@ -281,6 +288,7 @@ struct Work {
     double *M1, *M2, *bigA, *bigT, *vec, *kry;
     size_t n_M;                      // capacity of M1 / M2 of this lane
     TcScratch tcs;                   // tensor-core scratch (main lane, mixed updates)
+    TcScratch tcs2;                  // ... of the look-ahead lane
     GemmScratch gs2;
     double *M1b, *M2b;
 
@@ -315,7 +323,7 @@ struct Work {
         o.M1 = M1b;
         o.M2 = M2b;
         o.n_M = L.n_Mb;
-        o.tcs = TcScratch();
+        o.tcs = tcs2;
         return o;
     }
 };
@@ -370,6 +378,9 @@ void carve_work(gbqr_ctx *cx, char *base, const Layout &L, const Params &pr, con
     w->tcs.base = w->L.n_tc ? (void *)(base + w->L.tc) : nullptr;
     w->tcs.bytes = w->L.n_tc;
     w->tcs.err = &cx->dinfo->timeout;
+    w->tcs2.base = w->L.n_tc2 ? (void *)(base + w->L.tc2) : nullptr;
+    w->tcs2.bytes = w->L.n_tc2;
+    w->tcs2.err = &cx->dinfo->timeout;
 }
 
 // Arrival counters start at zero (every kernel leaves them zero again).
@@ -475,8 +486,12 @@ gbqr_status qr_eg(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, Real *T, 
     Real *M1 = w.m1<Real>(), *M2 = w.m2<Real>();
     const GemmScratchT<Real> gsr = w.gsr<Real>();
     TRY(qr_eg(w, m, n1, A, lda, T, ldt));                  // left recursion
-    // M1 = V_L^T A_R ; M2 = T_L^T M1 ; A_R -= V_L M2
-    TRY(apply_block(w, true, m, n2, n1, A, lda, T, ldt, AR, lda));
+    // M1 = V_L^T A_R ; M2 = T_L^T M1 ; A_R -= V_L M2.  On the mixed path the
+    // two tall products go to the tensor cores once they are large enough to
+    // beat the FP64 kernel's latency (the T-assembly below stays FP64, so T
+    // stays consistent with V and Q = I - V T V^T orthogonal to FP64 accuracy).
+    const int nsplit_in = (w.pr.nsplit > 0 && n1 >= kInPanelTcMinCols && m >= kInPanelTcMinRows) ? w.pr.nsplit : 0;
+    TRY(apply_block(w, true, m, n2, n1, A, lda, T, ldt, AR, lda, nsplit_in));
     // right recursion on B22
     Real *TR = T + n1 + n1 * ldt;
     TRY(qr_eg(w, m - n1, n2, A + n1 + n1 * lda, lda, TR, ldt));
@@ -807,6 +822,20 @@ gbqr_status gbqr::factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, 
 }
 
 extern "C" {
+
+gbqr_status gbqr_factor_f32(gbqr_ctx *cx, int64_t m, int64_t n, float *A, int64_t lda, float *T, int64_t ldt,
+                            int t_layout, const gbqr_opts *opts) {
+    if (!cx) return GBQR_EINVAL;
+    Params pr;
+    if (!resolve(opts, m, n, &pr) || pr.nsplit != 0) return GBQR_EINVAL;
+    TRY(check_layout_args(m, n, lda, ldt, t_layout, pr.nb));
+    if (n == 0) return GBQR_OK;
+    if (!A || !T) return GBQR_EINVAL;
+    if (is_host_pointer(A) || is_host_pointer(T)) return GBQR_EUNSUPPORTED;
+    Work w;
+    TRY(begin_work(cx, m, n, t_layout, pr, &w));
+    return factor_device(w, m, n, A, lda, T, ldt, t_layout);
+}
 
 static gbqr_status apply_entry(gbqr_ctx *cx, bool trans, int64_t m, int64_t n, const double *VR, int64_t lda,
                                const double *T, int64_t ldt, int layout, int64_t nb, int64_t nrhs,

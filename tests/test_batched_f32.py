@@ -97,3 +97,24 @@ def test_f32_rejects_tensor_core_updates(gb):
     with pytest.raises(gb.GbqrError):
         _run32(gb, ctx, [a], gb.opts(update_prec=gb.GBQR_MIXED_SPLITBF16))
     ctx.close()
+
+
+@pytest.mark.parametrize("m,n,layout_name,nb", [(3000, 700, "full", 0), (1500, 1500, "panel", 128),
+                                                (20000, 260, "panel", 64), (777, 97, "panel", 32)])
+def test_f32_single_factorization(gb, orc, m, n, layout_name, nb):
+    """gbqr_factor_f32: the FP32 instantiation of the whole QR-EG path (PANEL
+    with look-ahead, FULL with the T-merge), against the FP64 oracle on the
+    same float32-rounded input."""
+    import torch
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    a = workloads.gaussian(m, n, 600 + n).astype(np.float32)
+    ctx = gb.Context(0)
+    A = _device32(a)
+    nbr = nb or gb.default_panel_nb(m, n)
+    rows = n if layout == gb.GBQR_T_FULL else min(nbr, n)
+    T = torch.full((n, rows), float("nan"), dtype=torch.float32, device="cuda").T
+    ctx.factor(A, T, layout, gb.opts(panel_nb=nb))
+    torch.cuda.synchronize()
+    _gpu.compare_factor(a.astype(np.float64), A.cpu().numpy(), T.cpu().numpy(), layout, nbr, orc,
+                        f"fp32 {m}x{n}", fp32=True)
+    ctx.close()
