@@ -399,19 +399,32 @@ gbqr_status gemm(const Exec &ex, const GemmOpT<Real> &op, const GemmScratchT<Rea
     if (op.K <= 0) {
         if (op.beta == Real(1)) return GBQR_OK;
     }
-    const int BM = tile_for(op.M), BN = tile_for(op.N);
+    // A small output (the T products of Algorithm 2 are 64 x 64 x 64 at the
+    // panel's top node) on 64 x 64 tiles would run on a handful of SMs at one
+    // SM's FP64 rate (2 FMA/clock: ~60 us for 64^3): shrink the tiles until
+    // the output spans the SMs, then split K.
+    // (FP64 only: FP32 runs 64x faster per SM on this part, and the extra
+    // splits measured slower for the FP32 batch.)
+    constexpr bool fp64 = std::is_same<Real, double>::value;
+    int BM = tile_for(op.M), BN = tile_for(op.N);
+    auto count_tiles = [&](int bm, int bn) { return ((op.M + bm - 1) / bm) * ((op.N + bn - 1) / bn); };
+    while (fp64 && count_tiles(BM, BN) < ex.num_sms && (BM > 16 || BN > 16)) {
+        if (BM >= BN && BM > 16) BM /= 2;
+        else BN /= 2;
+    }
     const int64_t tm = (op.M + BM - 1) / BM, tn = (op.N + BN - 1) / BN;
     if (tm > 0x7fffffff || tn > 65535) return GBQR_EUNSUPPORTED;
     const int64_t tiles = tm * tn;
     const int64_t ktiles = (std::max<int64_t>(op.K, 0) + BK - 1) / BK;
 
-    // Split K when the output alone cannot fill the GPU.  Each split keeps at
-    // least 4 K-tiles; pick the split count whose CTA total wastes the least
-    // of the last wave.
+    // Split K when the output alone cannot fill the GPU: at least 4 K-tiles
+    // per split where K allows, one where it is short; pick the split count
+    // whose CTA total wastes the least of the last wave.
     int S = 1;
     const int64_t fill = 2LL * ex.num_sms;
-    if (tiles < fill && ktiles >= 8) {
-        const int64_t smax = std::min<int64_t>({ktiles / 4, (int64_t)kMaxSplitCtasPerSm * ex.num_sms / tiles, 512});
+    if (tiles < fill && ktiles >= (fp64 ? 2 : 8)) {
+        const int64_t per = (ktiles >= 32 || !fp64) ? 4 : 1;
+        const int64_t smax = std::min<int64_t>({ktiles / per, (int64_t)kMaxSplitCtasPerSm * ex.num_sms / tiles, 512});
         double best = -1.0;
         for (int64_t s = 1; s <= smax; ++s) {
             const double ctas = (double)(tiles * s);
