@@ -118,6 +118,7 @@ struct Layout {
     size_t tc = 0, n_tc = 0;                              // tensor-core slices (mixed updates)
     size_t tc2 = 0, n_tc2 = 0;                            // ... of the look-ahead lane's in-panel updates
     size_t kry = 0, n_kry = 0;                            // least squares, mixed: Krylov basis of the refinement
+    size_t dinv = 0, n_dinv = 0;                          // ... and inverses of R's diagonal blocks
     size_t total = 0;
     size_t n_partial = 0, n_gcount = 0, n_M = 0, n_Mb = 0, n_bigA = 0, n_bigT = 0, counter_bytes = 0;
     TsqrPlan tsqr;
@@ -176,6 +177,8 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     if (staging && pr.nsplit > 0) {
         L.n_kry = (size_t)(kKrylov + 2) * (size_t)(std::max<int64_t>(m, 1) + std::max<int64_t>(n, 1)) + 4 * (kKrylov + 2) + 16;
         L.kry = take(L.n_kry * 8);
+        L.n_dinv = (size_t)((std::max<int64_t>(n, 1) + kTrsvBlockSize - 1) / kTrsvBlockSize) * kTrsvBlockSize * kTrsvBlockSize;
+        L.dinv = take(L.n_dinv * 8);
     }
     L.total = off;
     return L;
@@ -285,7 +288,7 @@ struct Work {
     Params pr;
     GemmScratch gs;
     TsqrWork tw;
-    double *M1, *M2, *bigA, *bigT, *vec, *kry;
+    double *M1, *M2, *bigA, *bigT, *vec, *kry, *dinv;
     size_t n_M;                      // capacity of M1 / M2 of this lane
     TcScratch tcs;                   // tensor-core scratch (main lane, mixed updates)
     TcScratch tcs2;                  // ... of the look-ahead lane
@@ -368,6 +371,7 @@ void carve_work(gbqr_ctx *cx, char *base, const Layout &L, const Params &pr, con
     w->bigT = (double *)(base + w->L.bigT);
     w->vec = (double *)(base + w->L.vec);
     w->kry = w->L.n_kry ? (double *)(base + w->L.kry) : nullptr;
+    w->dinv = w->L.n_dinv ? (double *)(base + w->L.dinv) : nullptr;
     w->n_M = w->L.n_M;
     w->gs2.partial = (double *)(base + w->L.partial2);
     w->gs2.partial_elems = pr.lookahead ? w->L.n_partial : 0;
@@ -416,15 +420,8 @@ gbqr_status apply_block(Work &w, bool trans, int64_t mr, int64_t nc, int64_t kv,
     if (nc == 1) {
         // one vector: matrix-vector products instead of 1-column GEMM tiles
         TRY(gemv_t(w.ex, mr, kv, V, ldv, C, 1.0, 0.0, w.M1, MASK_UNIT_LOWER));
-        if (kv <= kThreads) {
-            TRY(trmv_upper(w.ex, (int)kv, T, ldt, trans, w.M1, w.M2));
-        } else {
-            GemmOp h;
-            h.M = kv; h.N = 1; h.K = kv;
-            h.A = T; h.lda = ldt; h.ta = trans; h.maskA = MASK_UPPER;
-            h.B = w.M1; h.ldb = kv; h.C = w.M2; h.ldc = kv;
-            TRY(gemm(w.ex, h, w.gs));
-        }
+        if (kv > 0x7fffffff) return GBQR_EUNSUPPORTED;
+        TRY(trmv_upper(w.ex, (int)kv, T, ldt, trans, w.M1, w.M2));
         return gemv_n(w.ex, mr, kv, V, ldv, w.M2, -1.0, 1.0, C, w.gs.partial, w.gs.partial_elems, MASK_UNIT_LOWER);
     }
     if (nsplit > 0 && w.tcs.base) {
@@ -919,7 +916,11 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     TRY(copy_matrix(w.ex, m, 1, b, m, f, m));
     TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, f, m, false));
     TRY(copy_matrix(w.ex, n, 1, f, n, x, n));
-    TRY(trsv_upper(w.ex, n, w.bigA, m, x, &di->rankdef));
+    // the mixed path solves with R a dozen times: invert its diagonal blocks
+    // once, and every block step becomes a small matrix-vector product
+    const double *dinv = (prec != GBQR_FP64) ? w.dinv : nullptr;
+    if (dinv) TRY(trsv_block_inverses(w.ex, n, w.bigA, m, w.dinv, &di->rankdef));
+    TRY(trsv_upper(w.ex, n, w.bigA, m, x, &di->rankdef, dinv));
     // Refinement on the augmented system K [r; x] = [b; 0], K = [I A; A^T 0],
     // with FP64 residuals.  The mixed QR solves K approximately (M^{-1}):
     //   h = R^{-T} g,  d = Q^T f,  dx = R^{-1} (d(0:n) - h),  dr = Q [h; d(n:m)].
@@ -965,11 +966,11 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     if (prec != GBQR_FP64) {
         auto precond = [&](double *fv, double *gv, double *dxv) -> gbqr_status {
             // in (fv, gv); out: dr in fv, dx in dxv; gv is overwritten (h)
-            TRY(trsv_upper_t(w.ex, n, w.bigA, m, gv, &di->rankdef));
+            TRY(trsv_upper_t(w.ex, n, w.bigA, m, gv, &di->rankdef, dinv));
             TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, fv, m, false));
             TRY(copy_matrix(w.ex, n, 1, fv, n, dxv, n));
             TRY(axpby(w.ex, n, -1.0, gv, 1.0, dxv));
-            TRY(trsv_upper(w.ex, n, w.bigA, m, dxv, &di->rankdef));
+            TRY(trsv_upper(w.ex, n, w.bigA, m, dxv, &di->rankdef, dinv));
             TRY(copy_matrix(w.ex, n, 1, gv, n, fv, n));
             return apply_q_any(w, false, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, fv, m, false);
         };

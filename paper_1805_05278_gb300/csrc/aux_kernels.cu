@@ -69,8 +69,17 @@ __global__ void __launch_bounds__(kThreads) gemv_n_partial_kernel(int64_t m, int
         if (i >= c0 && i < c1) acc = x[i];
         c1 = min(c1, i);
     }
-    for (int64_t j = c0; j < c1; ++j) acc = fma(A[i + j * lda], x[j], acc);
-    P[(int64_t)blockIdx.y * m + i] = acc;
+    // four independent chains: a dependent FP64 FMA costs ~100 cycles here
+    double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int64_t j = c0;
+    for (; j + 3 < c1; j += 4) {
+        acc = fma(A[i + j * lda], x[j], acc);
+        a1 = fma(A[i + (j + 1) * lda], x[j + 1], a1);
+        a2 = fma(A[i + (j + 2) * lda], x[j + 2], a2);
+        a3 = fma(A[i + (j + 3) * lda], x[j + 3], a3);
+    }
+    for (; j < c1; ++j) acc = fma(A[i + j * lda], x[j], acc);
+    P[(int64_t)blockIdx.y * m + i] = (acc + a1) + (a2 + a3);
 }
 
 __global__ void __launch_bounds__(kThreads) gemv_n_reduce_kernel(int64_t m, int nchunks, const double *P, double alpha,
@@ -82,23 +91,41 @@ __global__ void __launch_bounds__(kThreads) gemv_n_reduce_kernel(int64_t m, int 
     y[i] = (beta == 0.0) ? alpha * s : fma(beta, y[i], alpha * s);
 }
 
-// g(n) = alpha * A^T r + beta * g: one warp per column.
+// g(n) = alpha * A^T r + beta * g: one CTA per column, every thread on rows
+// strided by the block size in four independent chains (a single warp per
+// column ran an m/32-long dependent FMA chain at ~100 cycles a link).
 __global__ void __launch_bounds__(kThreads) gemv_t_kernel(int64_t m, int64_t n, const double *A, int64_t lda,
                                                          const double *r, double alpha, double beta, double *g,
                                                          int mask) {
-    const int lane = threadIdx.x & 31;
-    const int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ double red[kThreads / 32];
+    const int64_t j = blockIdx.x;
     if (j >= n) return;
-    double acc = 0.0;
+    const double *a = A + j * lda;
+    double acc = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int64_t i0 = 0;
     if (mask == MASK_UNIT_LOWER) {
-        if (lane == 0 && j < m) acc = r[j];
+        if (threadIdx.x == 0 && j < m) acc = r[j];
         i0 = j + 1;
     }
-    for (int64_t i = i0 + lane; i < m; i += 32) acc = fma(A[i + j * lda], r[i], acc);
+    const int64_t step = blockDim.x;
+    int64_t i = i0 + threadIdx.x;
+    for (; i + 3 * step < m; i += 4 * step) {
+        acc = fma(a[i], r[i], acc);
+        a1 = fma(a[i + step], r[i + step], a1);
+        a2 = fma(a[i + 2 * step], r[i + 2 * step], a2);
+        a3 = fma(a[i + 3 * step], r[i + 3 * step], a3);
+    }
+    for (; i < m; i += step) acc = fma(a[i], r[i], acc);
+    acc = (acc + a1) + (a2 + a3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) g[j] = (beta == 0.0) ? alpha * acc : fma(beta, g[j], alpha * acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        g[j] = (beta == 0.0) ? alpha * s : fma(beta, g[j], alpha * s);
+    }
 }
 
 // out[0] = sum x^2, out[1] = sum y^2 (one CTA, fixed order).
@@ -208,11 +235,84 @@ __device__ void warp_block_solve(int64_t jb, int s, const double *R, int64_t ldr
     __syncthreads();
 }
 
+// Inverses of the diagonal blocks of R (kTrsvBlock x kTrsvBlock, upper
+// triangular), one CTA per block, for the refinement's repeated solves with
+// the same R.  Bottom-up over block sizes 1, 2, 4, ...: for each pair of
+// adjacent diagonal blocks Ri12 = -Ri11 R12 Ri22, so the dependency depth is
+// log2 of the block size (a substitution would chain the whole block).
+__global__ void __launch_bounds__(kThreads) trsv_block_inverse_kernel(int64_t n, const double *R, int64_t ldr,
+                                                                    double *Dinv, long long *rankdef) {
+    constexpr int B = kTrsvBlock;
+    __shared__ double Rs[B * B], Ri[B * B], M[B * B];
+    const int64_t jb = (int64_t)blockIdx.x * B;
+    const int s = (int)((n - jb) < (int64_t)B ? (n - jb) : (int64_t)B);
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < B * B; idx += nthr) {
+        const int i = idx % B, c = idx / B;
+        Rs[idx] = (i < s && c < s && i <= c) ? R[(jb + i) + (jb + c) * ldr] : 0.0;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < B * B; idx += nthr) {
+        const int i = idx % B, c = idx / B;
+        double v = 0.0;
+        if (i == c && i < s) {
+            const double d = Rs[idx];
+            if (d == 0.0) atomicMin(rankdef, (long long)(jb + i));
+            v = 1.0 / d;
+        }
+        Ri[idx] = v;
+    }
+    __syncthreads();
+    for (int h = 1; h < B; h *= 2) {
+        const int h2 = 2 * h;
+        for (int idx = tid; idx < B * B; idx += nthr) {     // M = R12 Ri22
+            const int row = idx % B, col = idx / B;
+            const int b1 = (row / h2) * h2 + h;
+            if (row >= b1 || col < b1 || col >= b1 + h) continue;
+            double acc = 0.0;
+            for (int l = b1; l <= col; ++l) acc = fma(Rs[row + l * B], Ri[l + col * B], acc);
+            M[idx] = acc;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < B * B; idx += nthr) {     // Ri12 = -Ri11 M
+            const int row = idx % B, col = idx / B;
+            const int b1 = (row / h2) * h2 + h;
+            if (row >= b1 || col < b1 || col >= b1 + h) continue;
+            double acc = 0.0;
+            for (int l = row; l < b1; ++l) acc = fma(Ri[row + l * B], M[l + col * B], acc);
+            Ri[idx] = -acc;
+        }
+        __syncthreads();
+    }
+    double *D = Dinv + (size_t)blockIdx.x * B * B;
+    for (int idx = tid; idx < B * B; idx += nthr) D[idx] = Ri[idx];
+}
+
+// x(jb : jb+s) <- op(Di) x(jb : jb+s) for a block inverse Di (upper, ld B;
+// op = transpose for R^T): four threads per row, shuffles across the four.
+__device__ void block_inverse_apply(int64_t jb, int s, const double *Di, double *x, double *xs, bool transpose) {
+    constexpr int B = kTrsvBlock;
+    if (threadIdx.x < s) xs[threadIdx.x] = x[jb + threadIdx.x];
+    __syncthreads();
+    const int i = threadIdx.x >> 2, part = threadIdx.x & 3;
+    double acc = 0.0;
+    if (i < s) {
+        if (!transpose)
+            for (int c = i + part; c < s; c += 4) acc = fma(Di[i + c * B], xs[c], acc);
+        else
+            for (int c = part; c <= i; c += 4) acc = fma(Di[c + i * B], xs[c], acc);
+    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    if (i < s && part == 0) x[jb + i] = acc;
+}
+
 // Back substitution R x = c, one launch per block (from the bottom): apply
 // the just-solved block x(j0:j0+s) to rows [0, j0) - each CTA owns 256 rows -
 // then the CTA owning the block just above, rows [jn, j0), solves it.
 __global__ void __launch_bounds__(kThreads) trsv_step_kernel(int64_t j0, int s, int64_t jn, int sn, const double *R,
-                                                           int64_t ldr, double *x, long long *rankdef) {
+                                                           int64_t ldr, double *x, long long *rankdef,
+                                                           const double *Dinv) {
     __shared__ double xb[kTrsvBlock];
     __shared__ double xs[kTrsvBlock];
     __shared__ double Rs[kTrsvBlock * kTrsvBlock];
@@ -220,14 +320,25 @@ __global__ void __launch_bounds__(kThreads) trsv_step_kernel(int64_t j0, int s, 
     __syncthreads();
     const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
     if (i < j0 && s > 0) {
-        double acc = 0.0;
-        for (int l = 0; l < s; ++l) acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
-        x[i] -= acc;
+        double acc = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        int l = 0;
+        for (; l + 3 < s; l += 4) {
+            acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
+            a1 = fma(R[i + (j0 + l + 1) * ldr], xb[l + 1], a1);
+            a2 = fma(R[i + (j0 + l + 2) * ldr], xb[l + 2], a2);
+            a3 = fma(R[i + (j0 + l + 3) * ldr], xb[l + 3], a3);
+        }
+        for (; l < s; ++l) acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
+        x[i] -= (acc + a1) + (a2 + a3);
     }
     const int64_t r0 = (int64_t)blockIdx.x * kThreads;
     if (sn > 0 && jn >= r0 && jn < r0 + kThreads) {
         __syncthreads();                 // this CTA's rows [jn, j0) are final
         __threadfence_block();
+        if (Dinv) {
+            block_inverse_apply(jn, sn, Dinv + (size_t)(jn / kTrsvBlock) * kTrsvBlock * kTrsvBlock, x, xs, false);
+            return;
+        }
         if (threadIdx.x < sn) xs[threadIdx.x] = x[jn + threadIdx.x];
         __syncthreads();
         warp_block_solve(jn, sn, R, ldr, xs, Rs, false, rankdef);
@@ -240,7 +351,7 @@ __global__ void __launch_bounds__(kThreads) trsv_step_kernel(int64_t j0, int s, 
 // entries, one warp per entry - then the CTA owning the next block solves it.
 __global__ void __launch_bounds__(kThreads) trsv_t_step_kernel(int64_t n, int64_t jp, int sp, int sn,
                                                              const double *R, int64_t ldr, double *x,
-                                                             long long *rankdef) {
+                                                             long long *rankdef, const double *Dinv) {
     __shared__ double xb[kTrsvBlock];
     __shared__ double xs[kTrsvBlock];
     __shared__ double Rs[kTrsvBlock * kTrsvBlock];
@@ -262,6 +373,10 @@ __global__ void __launch_bounds__(kThreads) trsv_t_step_kernel(int64_t n, int64_
     if (blockIdx.x == 0 && sn > 0) {
         __syncthreads();
         __threadfence_block();
+        if (Dinv) {
+            block_inverse_apply(e0, sn, Dinv + (size_t)(e0 / kTrsvBlock) * kTrsvBlock * kTrsvBlock, x, xs, true);
+            return;
+        }
         if (threadIdx.x < sn) xs[threadIdx.x] = x[e0 + threadIdx.x];
         __syncthreads();
         warp_block_solve(e0, sn, R, ldr, xs, Rs, true, rankdef);
@@ -269,17 +384,22 @@ __global__ void __launch_bounds__(kThreads) trsv_t_step_kernel(int64_t n, int64_
     }
 }
 
-// y = op(T) w for a k x k upper triangular T (k <= kThreads), one CTA.
+// y = op(T) w for a k x k upper triangular T: one warp per output entry
+// (lanes split the row's dot product; a thread per row ran a k-long
+// dependent FMA chain).
 __global__ void __launch_bounds__(kThreads) trmv_kernel(int k, const double *T, int64_t ldt, bool trans,
                                                       const double *w, double *y) {
-    const int i = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
     if (i >= k) return;
     double acc = 0.0;
     if (!trans)
-        for (int l = i; l < k; ++l) acc = fma(T[i + (int64_t)l * ldt], w[l], acc);
+        for (int l = i + lane; l < k; l += 32) acc = fma(T[i + (int64_t)l * ldt], w[l], acc);
     else
-        for (int l = 0; l <= i; ++l) acc = fma(T[l + (int64_t)i * ldt], w[l], acc);
-    y[i] = acc;
+        for (int l = lane; l <= i; l += 32) acc = fma(T[l + (int64_t)i * ldt], w[l], acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[i] = acc;
 }
 
 unsigned grid_for(int64_t elems, int num_sms) {
@@ -324,7 +444,18 @@ template gbqr_status scan_nonfinite<double>(const Exec &, int64_t, int64_t, cons
 template gbqr_status scan_nonfinite<float>(const Exec &, int64_t, int64_t, const float *, int64_t,
                                            unsigned long long *);
 
-gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef) {
+gbqr_status trsv_block_inverses(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *Dinv,
+                                long long *rankdef) {
+    if (n <= 0) return GBQR_OK;
+    const int64_t nblk = (n + kTrsvBlock - 1) / kTrsvBlock;
+    trace_begin(ex, FAM_TRSV);
+    trsv_block_inverse_kernel<<<(unsigned)nblk, kThreads, 0, ex.stream>>>(n, R, ldr, Dinv, rankdef);
+    return trace_end(ex, FAM_TRSV, (double)nblk * kTrsvBlock * kTrsvBlock * kTrsvBlock / 3.0,
+                     8.0 * nblk * kTrsvBlock * kTrsvBlock * 2.0);
+}
+
+gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef,
+                       const double *Dinv) {
     if (n <= 0) return GBQR_OK;
     const int64_t nblk = (n + kTrsvBlock - 1) / kTrsvBlock;
     // launch k applies block k (solved) and solves block k-1; the first
@@ -336,13 +467,14 @@ gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, 
         const int sn = (int)std::min<int64_t>(kTrsvBlock, n - jn);
         const unsigned grid = (unsigned)std::max<int64_t>(1, (j0 + kThreads - 1) / kThreads);
         trace_begin(ex, FAM_TRSV);
-        trsv_step_kernel<<<grid, kThreads, 0, ex.stream>>>(j0, s, jn, sn, R, ldr, x, rankdef);
+        trsv_step_kernel<<<grid, kThreads, 0, ex.stream>>>(j0, s, jn, sn, R, ldr, x, rankdef, Dinv);
         TRY_ST(trace_end(ex, FAM_TRSV, 2.0 * j0 * s + (double)sn * sn, 8.0 * j0 * s));
     }
     return GBQR_OK;
 }
 
-gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef) {
+gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef,
+                         const double *Dinv) {
     if (n <= 0) return GBQR_OK;
     const int64_t nblk = (n + kTrsvBlock - 1) / kTrsvBlock;
     // launch k applies block k-1 (solved) and solves block k; the first
@@ -355,7 +487,7 @@ gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr
         const int64_t rest = n - (jp + sp);
         const unsigned grid = (unsigned)std::max<int64_t>(1, (rest + kTrsvBlock - 1) / kTrsvBlock);
         trace_begin(ex, FAM_TRSV);
-        trsv_t_step_kernel<<<grid, kThreads, 0, ex.stream>>>(n, jp, sp, sn, R, ldr, x, rankdef);
+        trsv_t_step_kernel<<<grid, kThreads, 0, ex.stream>>>(n, jp, sp, sn, R, ldr, x, rankdef, Dinv);
         TRY_ST(trace_end(ex, FAM_TRSV, 2.0 * rest * sp + (double)sn * sn, 8.0 * rest * sp));
     }
     return GBQR_OK;
@@ -363,9 +495,8 @@ gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr
 
 gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool trans, const double *w, double *y) {
     if (k <= 0) return GBQR_OK;
-    if (k > kThreads) return GBQR_EUNSUPPORTED;
     trace_begin(ex, FAM_GEMV);
-    trmv_kernel<<<1, kThreads, 0, ex.stream>>>(k, T, ldt, trans, w, y);
+    trmv_kernel<<<(unsigned)((k + kThreads / 32 - 1) / (kThreads / 32)), kThreads, 0, ex.stream>>>(k, T, ldt, trans, w, y);
     return trace_end(ex, FAM_GEMV, (double)k * k, 4.0 * k * k);
 }
 
@@ -389,9 +520,9 @@ gbqr_status gemv_n(const Exec &ex, int64_t m, int64_t n, const double *A, int64_
 gbqr_status gemv_t(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, const double *r, double alpha,
                    double beta, double *g, int mask) {
     if (n <= 0) return GBQR_OK;
-    const int per = kThreads / 32;
+    if (n > 0x7fffffff) return GBQR_EUNSUPPORTED;
     trace_begin(ex, FAM_GEMV);
-    gemv_t_kernel<<<(unsigned)((n + per - 1) / per), kThreads, 0, ex.stream>>>(m, n, A, lda, r, alpha, beta, g, mask);
+    gemv_t_kernel<<<(unsigned)n, kThreads, 0, ex.stream>>>(m, n, A, lda, r, alpha, beta, g, mask);
     return trace_end(ex, FAM_GEMV, 2.0 * m * n, 8.0 * m * n);
 }
 

@@ -147,11 +147,18 @@ gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const Real *A, 
                            unsigned long long *flag);
 // x (n) <- R^{-1} x, R upper triangular n x n (ldr); records the first zero
 // diagonal index (or leaves *rankdef untouched) via atomicMin.
+// Dinv (optional): inverses of R's 64 x 64 diagonal blocks from
+// trsv_block_inverses; each block step is then a small matrix-vector product
+// instead of a substitution chain (the mixed path's repeated solves).
 gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x,
-                       long long *rankdef);
+                       long long *rankdef, const double *Dinv = nullptr);
+gbqr_status trsv_block_inverses(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *Dinv,
+                                long long *rankdef);
+constexpr int kTrsvBlockSize = 64;
 
 // x (n) <- R^{-T} x (forward substitution with the lower triangle R^T).
-gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef);
+gbqr_status trsv_upper_t(const Exec &ex, int64_t n, const double *R, int64_t ldr, double *x, long long *rankdef,
+                         const double *Dinv = nullptr);
 // y = alpha A x + beta y (A m x n); partial: >= m * chunks doubles of scratch.
 // mask MASK_UNIT_LOWER treats A as a unit lower trapezoidal basis.
 gbqr_status gemv_n(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, const double *x, double alpha,
