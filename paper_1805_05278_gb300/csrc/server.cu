@@ -41,14 +41,14 @@ struct Record {
     Clock::time_point t_submit, t_start, t_done;
 };
 
-// GBQR_PREC_AUTO: the tensor-core updates only pay off where the trailing
-// update GEMMs dominate the solve.  Measured single-solve times (graded
-// columns, kappa ~ 1e4): mixed / FP64 = 1.5x faster at 65536 x 1024, 1.19x at
-// 16384 x 1024, even at 65536 x 512 (m n^2 = 1.7e10), slower below (the
-// FP64 panel factorizations dominate and the refinement adds its GMRES
-// steps; with n <= 128 there is no trailing update at all).
+// GBQR_PREC_AUTO: the tensor-core updates only pay off where the update
+// GEMMs dominate the solve.  Measured single-solve speed-ups of the mixed
+// path over FP64 (graded columns, kappa ~ 1e4): 2.44x at 65536 x 1024, 1.62x
+// at 65536 x 512, 1.19x at 16384 x 512, 1.17x at 65536 x 256, 1.04x at
+// 4096 x 1024 (all m n^2 >= 4e9), even at 16384 x 256, slower below (the FP64
+// panel chain dominates and the refinement adds its GMRES steps).
 int auto_precision(int64_t m, int64_t n) {
-    return (n >= 512 && (double)m * n * n >= 1.5e10) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
+    return (n >= 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
 }
 
 // Workspace of gbqr_ls_solve for this request: its shape and precision, with
