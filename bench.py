@@ -72,6 +72,8 @@ def parse():
     p.add_argument("--batched-autotune-ms", type=float, default=20000.0,
                    help="budget of gbqr_autotune_batched for the batched measurement (0: defaults)")
     p.add_argument("--panel", type=int, default=0)
+    p.add_argument("--lookahead", choices=["on", "off"], default=None,
+                   help="look-ahead of the PANEL top level (default: on, or the tuner's choice)")
     p.add_argument("--leaf", type=int, default=0)
     p.add_argument("--fanout", type=int, default=0)
     p.add_argument("--ls-solves", type=int, default=3, help="timed least-squares solves per grid point and precision (0: skip)")
@@ -465,12 +467,14 @@ def run_gbqr(args):
     w = workloads.WORKLOADS[args.workload]
     layout = gb.GBQR_T_PANEL if args.layout == "panel" else gb.GBQR_T_FULL
     o = gb.opts(cutoff_b=args.cutoff, panel_nb=args.panel, leaf_rows=args.leaf, fanout=args.fanout,
+                lookahead={None: 0, "on": 1, "off": -1}[args.lookahead],
                 fp64_gemm=gb.GBQR_GEMM_DMMA if args.fp64_gemm == "dmma" else gb.GBQR_GEMM_DFMA)
     stream = torch.cuda.current_stream(dev)
     ctx = gb.Context(dev, stream)
     # the tuner picks (b, k, leaf, nb, look-ahead, GEMM engine) unless any is given
     tuned, tune_ms = None, None
-    explicit = args.cutoff or args.panel or args.leaf or args.fanout or args.fp64_gemm != "dfma"
+    explicit = (args.cutoff or args.panel or args.leaf or args.fanout or args.fp64_gemm != "dfma"
+                or args.lookahead is not None)
     if args.autotune_ms > 0 and not explicit:
         o, tune_ms = ctx.autotune(w.m, w.n, layout, gb.GBQR_FP64, args.autotune_ms)
         tuned = gb.opts_dict(o)
