@@ -63,6 +63,8 @@ def parse():
     p.add_argument("--impl", default="gbqr", choices=["gbqr", "reference"])
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                   help="skip the backward-error / orthogonality check after the timed region")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cutoff", type=int, default=0)
     p.add_argument("--fp64-gemm", choices=["dmma", "dfma"], default="dfma",
@@ -538,6 +540,24 @@ def run_gbqr(args):
             e2e_times.append(dt)
     e2e_value = w.flops * world / statistics.median(e2e_times) / 1e12 if e2e_times else None
 
+    # accuracy of the last timed factorization (measurement only: torch on
+    # the device): Q from gbqr_form_q, backward error and orthogonality (F-norm)
+    accuracy = None
+    if args.accuracy and w.m >= w.n:
+        try:
+            Q = gb.colmajor(w.m, w.n, f"cuda:{dev}")
+            ctx.form_q(A, T, Q, layout, nb)
+            torch.cuda.synchronize()
+            R = torch.triu(A[:w.n, :])
+            bwd = float(torch.linalg.matrix_norm(A0 - Q @ R) / torch.linalg.matrix_norm(A0))
+            QtQ = Q.T @ Q
+            QtQ.diagonal().sub_(1.0)
+            accuracy = {"backward_err_fro": bwd, "orthogonality_fro": float(torch.linalg.matrix_norm(QtQ)),
+                        "note": "||A - QR||_F / ||A||_F and ||Q^T Q - I||_F of the last timed step, FP64"}
+            del Q, R, QtQ
+        except (gb.GbqrError, RuntimeError) as exc:
+            accuracy = {"error": str(exc)}
+
     st, info = ctx.sync()
     ls = measure_ls(gb, None, dev, args) if (args.ls_solves > 0 and rank == 0) else None
     batched = measure_batched(gb, dev, args) if (args.batched > 0 and rank == 0) else None
@@ -590,6 +610,7 @@ def run_gbqr(args):
             "ls": ls,
             "batched": batched,
             "serving": serving,
+            "accuracy": accuracy,
             "status_after": int(st),
         }
         print(json.dumps(line), flush=True)
