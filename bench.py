@@ -48,7 +48,7 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 # traffic is null for any configuration without a capture.
 DGEMM_TRAFFIC_PER_LAUNCH = {
     # (workload, panel_nb, cutoff_b, fanout, leaf_rows, lookahead, engine): bytes
-    ("graded_8192x8192", 64, 16, 8, 0, 1, "dfma"): 21.73e6,
+    ("graded_8192x8192", 128, 16, 8, 0, 1, "dfma"): 11.69e6,
 }
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs peak; LS solves/s, p99 ms: mixed vs FP64"
 
