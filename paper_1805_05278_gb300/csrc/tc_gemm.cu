@@ -28,6 +28,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 namespace gbqr {
@@ -446,13 +447,15 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
     if (!make_map(&mA, As, K, op.M, op.nsplit, ldk, TC_BM) || !make_map(&mB, Bs, K, op.N, op.nsplit, ldk, BN))
         return GBQR_ECUDA;
     const size_t smem = tc_smem_bytes(BN);
-    static bool attr[64][2] = {};
+    // per device and tile width, once (server workers launch from several threads)
+    static std::atomic<bool> attr[64][2];
     const int bi = BN == 128 ? 1 : 0;
-    if (ex.device >= 0 && ex.device < 64 && !attr[ex.device][bi]) {
+    const bool cached = ex.device >= 0 && ex.device < 64;
+    if (!cached || !attr[ex.device][bi].load(std::memory_order_acquire)) {
         cudaError_t e = (BN == 128) ? cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
                                     : cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return GBQR_ECUDA;
-        attr[ex.device][bi] = true;
+        if (cached) attr[ex.device][bi].store(true, std::memory_order_release);
     }
     dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)S);
     trace_begin(ex, FAM_TC_GEMM);

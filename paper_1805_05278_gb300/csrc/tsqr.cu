@@ -27,6 +27,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace gbqr {
 namespace {
@@ -672,14 +673,15 @@ gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, Real *A, int64_t lda,
     p.counters = work.counters;
     p.Tout = Tout; p.ldt = ldt;
 
-    static bool attr_done[64] = {false};
-    if (ex.device >= 0 && ex.device < 64 && !attr_done[ex.device]) {
+    // per device and scalar type, once (server workers launch from several threads)
+    static std::atomic<bool> attr_done[64];
+    if (!(ex.device >= 0 && ex.device < 64) || !attr_done[ex.device].load(std::memory_order_acquire)) {
         const int cap = (int)kSmemCap;
         if (cudaFuncSetAttribute(tsqr_up_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
             cudaFuncSetAttribute(tsqr_down_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
             cudaFuncSetAttribute(tsqr_recon_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
             return GBQR_ECUDA;
-        attr_done[ex.device] = true;
+        if (ex.device >= 0 && ex.device < 64) attr_done[ex.device].store(true, std::memory_order_release);
     }
     const double w = pl.w, mp = (double)pl.mp;
     const double ww = w * w;
