@@ -204,14 +204,21 @@ __device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, Rea
                 __syncwarp();
                 warp_pivot(S, ldS, nxt, rows, tau);
             }
-        } else {
-            // every other column (not j, not j+1) to the other warps, round robin
+        } else if (nw < 8 || wid != (pw + 4) % nw) {
+            // every other column (not j, not j+1) to the other warps, round
+            // robin - except the warp that shares the pivot warp's SM
+            // sub-partition (warp i runs on sub-partition i % 4): the pivot
+            // chain is bound by its FP64 issue slots, and a worker beside it
+            // would take them
             const int nexcl = (nxt < w) ? 2 : 1;
             const int ncols = w - nexcl;
-            const int me = (wid - pw - 1 + nw) % nw;  // 0 .. nw-2
+            const int partner = (nw >= 8) ? (pw + 4) % nw : -1;
+            const int nwork = (nw >= 8) ? nw - 2 : nw - 1;
+            int me = (wid - pw - 1 + nw) % nw;        // 0 .. nw-2
+            if (partner >= 0 && me > (partner - pw - 1 + nw) % nw) --me;   // skip the partner's slot
             int cols[4] = {0, 0, 0, 0};
             int g = 0;
-            for (int t = me; t < ncols; t += nw - 1) {
+            for (int t = me; t < ncols; t += nwork) {
                 cols[g++] = (t < j) ? t : t + nexcl;
                 if (g == 4) { warp_apply<4>(S, ldS, j, rows, cols, tj, G, w); g = 0; }
             }
