@@ -274,14 +274,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // C = beta * C + alpha * sum_z P[z] (FP64 accumulation of FP32 partials).
+// 2-D grid: x over rows m, y over columns n (no 64-bit division per entry).
 __global__ void __launch_bounds__(kThreads) tc_reduce_kernel(int M, int N, int S, const float *P, double *C,
                                                            int64_t ldc, double alpha, double beta) {
     const int64_t total = (int64_t)M * N;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    for (int n = blockIdx.y; n < N; n += gridDim.y) {
+        const int64_t e = m + (int64_t)n * M;
         double s = 0.0;
         for (int z = 0; z < S; ++z) s += (double)P[(size_t)z * total + e];
-        const int64_t m = e % M, n = e / M;
-        double *cp = C + m + n * ldc;
+        double *cp = C + m + (int64_t)n * ldc;
         double out = alpha * s;
         if (beta != 0.0) out = fma(beta, *cp, out);
         *cp = out;
@@ -298,13 +301,24 @@ __device__ __forceinline__ double masked_at(const double *X, int64_t ld, int64_t
     return X[r + c * ld];
 }
 
-__device__ __forceinline__ void split_store(double x, int ns, __nv_bfloat16 *dst, size_t slice_stride) {
-    double r = x;
-    for (int s = 0; s < ns; ++s) {
-        const __nv_bfloat16 h = __double2bfloat16(r);
-        dst[s * slice_stride] = h;
-        r -= (double)__bfloat162float(h);
+// Slices of x: the s <= 3 BF16 pieces carry 24 significant bits between
+// them, which FP32 holds, so the recurrence r -= bf16(r) runs in FP32 (exact
+// subtractions; this part issues FP32 at 64x its FP64 rate) after one
+// rounding of x to FP32.
+__device__ __forceinline__ void split_slices(double x, int ns, __nv_bfloat16 (&h)[3]) {
+    float r = (float)x;
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        h[s] = __float2bfloat16_rn(r);
+        r -= __bfloat162float(h[s]);
+        if (s + 1 >= ns) break;
     }
+}
+
+__device__ __forceinline__ void split_store(double x, int ns, __nv_bfloat16 *dst, size_t slice_stride) {
+    __nv_bfloat16 h[3];
+    split_slices(x, ns, h);
+    for (int s = 0; s < ns; ++s) dst[s * slice_stride] = h[s];
 }
 
 // BF16 slices of an FP64 operand, K-major for the MMA: operand row i holds
@@ -312,14 +326,29 @@ __device__ __forceinline__ void split_store(double x, int ns, __nv_bfloat16 *dst
 //   !transpose: operand (i, k) = stored (k, i)   (stored K x R, column-major)
 //    transpose: operand (i, k) = stored (i, k)   (stored R x K, column-major)
 // Entries k in [K, ldd) are zero.  mask applies to the stored coordinates.
+// 2-D grid: x over K in chunks of 4 consecutive entries per thread (one
+// 8-byte store of four BF16 per slice; ldd is a multiple of 8), y over rows.
 __global__ void __launch_bounds__(kThreads) split_plain_kernel(int64_t K, int64_t R, const double *src, int64_t lds,
                                                              int mask, int ns, __nv_bfloat16 *dst, int64_t ldd,
                                                              size_t slice_stride) {
-    const int64_t total = R * ldd;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = e % ldd, i = e / ldd;
-        const double x = (k < K) ? masked_at(src, lds, k, i, mask) : 0.0;
-        split_store(x, ns, dst + i * ldd + k, slice_stride);
+    const int64_t k0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (k0 >= ldd) return;
+    for (int64_t i = blockIdx.y; i < R; i += gridDim.y) {
+        __nv_bfloat16 h[4][3];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t k = k0 + q;
+            const double x = (k < K) ? masked_at(src, lds, k, i, mask) : 0.0;
+            split_slices(x, ns, h[q]);
+        }
+        for (int s = 0; s < ns; ++s) {
+            __nv_bfloat162 lo = __halves2bfloat162(h[0][s], h[1][s]);
+            __nv_bfloat162 hi = __halves2bfloat162(h[2][s], h[3][s]);
+            uint2 v;
+            v.x = *reinterpret_cast<uint32_t *>(&lo);
+            v.y = *reinterpret_cast<uint32_t *>(&hi);
+            *reinterpret_cast<uint2 *>(dst + s * slice_stride + i * ldd + k0) = v;
+        }
     }
 }
 
@@ -400,21 +429,20 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
 
     // slices of op(A) (rows M) and of B (rows N), K-major
     trace_begin(ex, FAM_OTHER);
+    auto plain_grid = [&](int64_t rows) {
+        return dim3((unsigned)((ldk / 4 + kThreads - 1) / kThreads), (unsigned)std::min<int64_t>(std::max<int64_t>(rows, 1), 65535));
+    };
     if (op.ta) {
-        const int64_t total = op.M * ldk;
-        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ex.num_sms * 16));
-        split_plain_kernel<<<g, kThreads, 0, ex.stream>>>(op.K, op.M, op.A, op.lda, op.maskA, op.nsplit, As, ldk, sa);
+        split_plain_kernel<<<plain_grid(op.M), kThreads, 0, ex.stream>>>(op.K, op.M, op.A, op.lda, op.maskA, op.nsplit,
+                                                                          As, ldk, sa);
     } else {
         dim3 g((unsigned)((ldk + 31) / 32), (unsigned)((op.M + 31) / 32));
         split_transpose_kernel<<<g, kThreads, 0, ex.stream>>>(op.K, op.M, op.A, op.lda, op.maskA, op.nsplit, As, ldk, sa);
     }
     TRY_ST(trace_end(ex, FAM_OTHER, 0.0, (8.0 + 2.0 * op.nsplit) * op.M * K));
     trace_begin(ex, FAM_OTHER);
-    {
-        const int64_t total = op.N * ldk;
-        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ex.num_sms * 16));
-        split_plain_kernel<<<g, kThreads, 0, ex.stream>>>(op.K, op.N, op.B, op.ldb, op.maskB, op.nsplit, Bs, ldk, sb);
-    }
+    split_plain_kernel<<<plain_grid(op.N), kThreads, 0, ex.stream>>>(op.K, op.N, op.B, op.ldb, op.maskB, op.nsplit,
+                                                                      Bs, ldk, sb);
     TRY_ST(trace_end(ex, FAM_OTHER, 0.0, (8.0 + 2.0 * op.nsplit) * op.N * K));
 
     // tile shape and split-K
@@ -466,7 +494,7 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
     if (S > 1) {
         trace_begin(ex, FAM_OTHER);
         const int64_t total = op.M * op.N;
-        const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)ex.num_sms * 16));
+        const dim3 g((unsigned)((op.M + kThreads - 1) / kThreads), (unsigned)std::min<int64_t>(op.N, 65535));
         tc_reduce_kernel<<<g, kThreads, 0, ex.stream>>>((int)op.M, (int)op.N, S, partial, op.C, op.ldc, op.alpha, op.beta);
         TRY_ST(trace_end(ex, FAM_OTHER, (double)S * total, 4.0 * S * total + 16.0 * total));
     }
