@@ -11,40 +11,31 @@ namespace {
 
 // Grid-stride over an m x n column-major matrix, one thread per element,
 // consecutive threads on consecutive rows (coalesced).
+// Elementwise kernels over an m x n column-major matrix: a 2-D grid, x
+// striding rows and y striding columns (no 64-bit division per entry).
+#define FOR_EACH_ENTRY(m, n, body)                                                                      \
+    for (int64_t j = blockIdx.y; j < (n); j += gridDim.y)                                               \
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (m); i += (int64_t)gridDim.x * blockDim.x) \
+            body
+
 __global__ void __launch_bounds__(kThreads) fill_identity_kernel(int64_t m, int64_t n, double *Q, int64_t ldq) {
-    const int64_t total = m * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % m, j = e / m;
-        Q[i + j * ldq] = (i == j) ? 1.0 : 0.0;
-    }
+    FOR_EACH_ENTRY(m, n, { Q[i + j * ldq] = (i == j) ? 1.0 : 0.0; })
 }
 
 __global__ void __launch_bounds__(kThreads) zero_strict_lower_kernel(int64_t n, double *T, int64_t ldt) {
-    const int64_t total = n * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % n, j = e / n;
-        if (i > j) T[i + j * ldt] = 0.0;
-    }
+    FOR_EACH_ENTRY(n, n, { if (i > j) T[i + j * ldt] = 0.0; })
 }
 
 __global__ void __launch_bounds__(kThreads) copy_kernel(int64_t m, int64_t n, const double *src, int64_t lds,
                                                       double *dst, int64_t ldd) {
-    const int64_t total = m * n;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % m, j = e / m;
-        dst[i + j * ldd] = src[i + j * lds];
-    }
+    FOR_EACH_ENTRY(m, n, { dst[i + j * ldd] = src[i + j * lds]; })
 }
 
 template <class Real>
 __global__ void __launch_bounds__(kThreads) nonfinite_kernel(int64_t m, int64_t n, const Real *A, int64_t lda,
                                                            unsigned long long *flag) {
-    const int64_t total = m * n;
     int bad = 0;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e % m, j = e / m;
-        bad |= !isfinite(A[i + j * lda]);
-    }
+    FOR_EACH_ENTRY(m, n, { bad |= !isfinite(A[i + j * lda]); })
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1ull);
 }
 
@@ -402,6 +393,14 @@ __global__ void __launch_bounds__(kThreads) trmv_kernel(int k, const double *T, 
     if (lane == 0) y[i] = acc;
 }
 
+// Grid of the elementwise kernels: enough row blocks to cover a column, and
+// columns until about 32 CTAs per SM.
+dim3 grid2d(int64_t m, int64_t n, int num_sms) {
+    const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((m + kThreads - 1) / kThreads, (int64_t)num_sms * 8));
+    const int64_t gy = std::max<int64_t>(1, std::min<int64_t>({n, (int64_t)65535, (int64_t)num_sms * 32 / gx + 1}));
+    return dim3((unsigned)gx, (unsigned)gy);
+}
+
 unsigned grid_for(int64_t elems, int num_sms) {
     const int64_t want = (elems + kThreads - 1) / kThreads;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms * 8));
@@ -412,14 +411,14 @@ unsigned grid_for(int64_t elems, int num_sms) {
 gbqr_status fill_identity(const Exec &ex, int64_t m, int64_t n, double *Q, int64_t ldq) {
     if (m <= 0 || n <= 0) return GBQR_OK;
     trace_begin(ex, FAM_OTHER);
-    fill_identity_kernel<<<grid_for(m * n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, Q, ldq);
+    fill_identity_kernel<<<grid2d(m, n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, Q, ldq);
     return trace_end(ex, FAM_OTHER, 0.0, 8.0 * m * n);
 }
 
 gbqr_status zero_strict_lower(const Exec &ex, int64_t n, double *T, int64_t ldt) {
     if (n <= 1) return GBQR_OK;
     trace_begin(ex, FAM_OTHER);
-    zero_strict_lower_kernel<<<grid_for(n * n, ex.num_sms), kThreads, 0, ex.stream>>>(n, T, ldt);
+    zero_strict_lower_kernel<<<grid2d(n, n, ex.num_sms), kThreads, 0, ex.stream>>>(n, T, ldt);
     return trace_end(ex, FAM_OTHER, 0.0, 4.0 * n * n);
 }
 
@@ -427,7 +426,7 @@ gbqr_status copy_matrix(const Exec &ex, int64_t m, int64_t n, const double *src,
                         double *dst, int64_t ldd) {
     if (m <= 0 || n <= 0) return GBQR_OK;
     trace_begin(ex, FAM_OTHER);
-    copy_kernel<<<grid_for(m * n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, src, lds, dst, ldd);
+    copy_kernel<<<grid2d(m, n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, src, lds, dst, ldd);
     return trace_end(ex, FAM_OTHER, 0.0, 16.0 * m * n);
 }
 
@@ -436,7 +435,7 @@ gbqr_status scan_nonfinite(const Exec &ex, int64_t m, int64_t n, const Real *A, 
                            unsigned long long *flag) {
     if (m <= 0 || n <= 0) return GBQR_OK;
     trace_begin(ex, FAM_OTHER);
-    nonfinite_kernel<Real><<<grid_for(m * n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, A, lda, flag);
+    nonfinite_kernel<Real><<<grid2d(m, n, ex.num_sms), kThreads, 0, ex.stream>>>(m, n, A, lda, flag);
     return trace_end(ex, FAM_OTHER, 0.0, (double)sizeof(Real) * m * n);
 }
 template gbqr_status scan_nonfinite<double>(const Exec &, int64_t, int64_t, const double *, int64_t,
