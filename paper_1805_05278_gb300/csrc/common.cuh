@@ -114,7 +114,7 @@ struct TsqrPlan {
     int ldS = 0;        // up kernel shared-memory leading dimension (>= hmax, >= k*w)
     int ldW = 0;        // down / recon kernels shared-memory leading dimension (>= hmax)
     int64_t nodes = 0;  // leaves + internal nodes
-    size_t smem_up = 0, smem_down = 0, smem_recon = 0;
+    size_t smem_up = 0, smem_down = 0;
     // workspace element counts
     size_t nR = 0, nT = 0, nY = 0, nX = 0, ncount = 0;
 };

@@ -9,15 +9,16 @@
 //                      same launch: the last CTA to arrive at a node (atomic
 //                      arrival counter) factors the stacked upper triangles
 //                      of its children; no CTA ever waits on another.
-//   tsqr_down_kernel   (Appendix C.2, downsweep): every CTA walks from the
-//                      root to its leaf applying the node Q-factors to
-//                      B^(L) = I, then forms its rows W_p of the leading w
-//                      columns of Q.
-//   tsqr_recon_kernel  (Appendix C.2, reconstruction): X + S = LU of the top
-//                      w x w block of W with S_jj = sgn(X^_jj) added before
-//                      eliminating column j; T = U S L^{-T}, R = -S R^(L),
-//                      V_top = L, and V_p = W_p U^{-1} for every other row.
-//                      The small LU is repeated by every CTA instead of being
+//   tsqr_down_kernel   (Appendix C.2, downsweep and reconstruction, one
+//                      launch): every CTA walks from the root to leaf 0 and
+//                      forms the top w x w block X of W = Q [I; 0] (from the
+//                      copy of leaf 0's top V block the upsweep kept), factors
+//                      X + S = LU with S_jj = sgn(X^_jj) added before
+//                      eliminating column j, walks to its own leaf applying
+//                      the node Q-factors to B^(L) = I, forms its rows W_p
+//                      and writes V_p = W_p U^{-1}; CTA 0 writes T = U S L^{-T},
+//                      V_top = L and R = -S R^(L).  The small LU and the walk
+//                      to leaf 0 are repeated by every CTA instead of being
 //                      broadcast, so the launch needs no inter-CTA waiting.
 //
 // Merged nodes exploit the structure of stacked triangles: the Householder
@@ -290,9 +291,16 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
     householder_block(S, ldS, w, LeafRows{h}, tau, G);
 
     // V_p (strict lower) and R_p (upper) back to the panel rows, R_p to the tree;
-    // then T_p, with the leaf block's shared memory as scratch.
+    // then T_p, with the leaf block's shared memory as scratch.  Leaf 0 also
+    // keeps a copy of its top w x w block of V: every CTA of the downsweep
+    // reads it to form X while CTA 0 overwrites those rows of the panel.
     for (int c = 0; c < w; ++c)
         for (int r = tid; r < h; r += nthr) p.A[(r0 + r) + c * p.lda] = S[(size_t)c * ldS + r];
+    if (leaf == 0)
+        for (int idx = tid; idx < w * w; idx += nthr) {
+            const int i = idx % w, c = idx / w;
+            p.wsX[idx] = (i > c) ? S[(size_t)c * ldS + i] : Real(0);
+        }
     {
         Real *Rn = p.wsR + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) {
@@ -372,104 +380,6 @@ __device__ void upper_upper(const Real *A, const Real *B, Real *C, int w, Real s
     }
 }
 
-// Downsweep.  Starting from B = I at the root, each node on the path gives
-// its child [B_0; B_1; ...] = (I - V T V^T)[B; 0] = [B - T B; -Y_1 T B; ...].
-// T, Y and I are upper triangular, so every B stays upper triangular and each
-// product costs about w^3/6 multiply-adds.
-template <class Real>
-__global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real *smem = reinterpret_cast<Real *>(smem_raw);
-    const int w = p.w, ldS = p.ldW, tid = threadIdx.x, nthr = blockDim.x;
-    const size_t ww = (size_t)w * w;
-    Real *B = smem;
-    Real *C = B + ww;
-    Real *M = C + ww;      // node T / Y, then leaf T_p and products
-    Real *Vs = M + ww;     // leaf block, ldS x w
-
-    const int leaf = blockIdx.x;
-    const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
-    const int h = (int)(r1 - r0);
-
-    int anc[41], Nlev[41];
-    int64_t offl[41];
-    anc[0] = leaf; Nlev[0] = p.P; offl[0] = 0;
-    for (int lv = 0; lv < p.L; ++lv) {
-        anc[lv + 1] = anc[lv] / p.k;
-        Nlev[lv + 1] = (Nlev[lv] + p.k - 1) / p.k;
-        offl[lv + 1] = offl[lv] + Nlev[lv];
-    }
-    for (int idx = tid; idx < w * w; idx += nthr) B[idx] = (idx % w == idx / w) ? Real(1) : Real(0);
-    __syncthreads();
-    for (int lv = p.L - 1; lv >= 0; --lv) {
-        const int parent = anc[lv + 1], first = parent * p.k;
-        const int cnt = min(p.k, Nlev[lv] - first);
-        if (cnt == 1) continue;
-        const int pos = anc[lv] - first;
-        const int64_t pidx = offl[lv + 1] + parent;
-        const Real *Tn = p.wsT + (size_t)pidx * ww;
-        for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tn[idx];
-        __syncthreads();
-        upper_upper(M, B, C, w, Real(1));          // C = T_node B
-        __syncthreads();
-        if (pos == 0) {
-            for (int idx = tid; idx < w * w; idx += nthr) B[idx] -= C[idx];
-        } else {
-            const Real *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos - 1)) * ww;
-            for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Yn[idx];
-            __syncthreads();
-            upper_upper(M, C, B, w, -Real(1));     // B = -Y_pos C
-        }
-        __syncthreads();
-    }
-
-    // leaf: W_p = (I - V_p T_p V_p^T) [B; 0]
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < h; r += nthr) Vs[(size_t)c * ldS + r] = p.A[(r0 + r) + c * p.lda];
-    {
-        const Real *Tp = p.wsT + (size_t)leaf * ww;
-        for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tp[idx];
-    }
-    __syncthreads();
-    // C = V1^T B, V1 = unit lower top w x w of the leaf block; B upper -> C upper
-    for (int idx = tid; idx < w * w; idx += nthr) {
-        const int i = idx % w, c = idx / w;
-        Real s = Real(0);
-        if (i <= c) {
-            s = B[i + c * w];
-            for (int l = i + 1; l <= c; ++l) s = rfma(Vs[(size_t)i * ldS + l], B[l + c * w], s);
-        }
-        C[idx] = s;
-    }
-    __syncthreads();
-    {
-        // Z = T_p C into registers, then over M after a barrier
-        Real z2[(kMaxPanel * kMaxPanel + kThreads - 1) / kThreads];
-        int q = 0;
-        for (int idx = tid; idx < w * w; idx += nthr, ++q) {
-            const int i = idx % w, c = idx / w;
-            Real s = Real(0);
-            for (int l = i; l <= c; ++l) s = rfma(M[i + l * w], C[l + c * w], s);
-            z2[q] = s;
-        }
-        __syncthreads();
-        q = 0;
-        for (int idx = tid; idx < w * w; idx += nthr, ++q) M[idx] = z2[q];
-    }
-    __syncthreads();
-    // W(r, c) = [B; 0](r, c) - sum_{i <= min(r, c)} Vhat(r, i) Z(i, c), Z upper
-    for (int idx = tid; idx < h * w; idx += nthr) {
-        const int r = idx % h, c = idx / h;
-        const int iend = min(r, c + 1);
-        Real s = Real(0);
-        for (int i = 0; i < iend; ++i) s = rfma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
-        if (r <= c) s += M[r + c * w];
-        const Real wv = ((r < w) ? B[r + c * w] : Real(0)) - s;
-        p.A[(r0 + r) + c * p.lda] = wv;
-        if (leaf == 0 && r < w) p.wsX[r + c * w] = wv;
-    }
-}
-
 // Inverse of the unit lower triangular L (ld w) into Li (ld w), blocked
 // bottom-up like build_t: Li21 = -Li22 L21 Li11 for each pair of blocks.
 template <class Real>
@@ -503,28 +413,123 @@ __device__ void unit_lower_inverse(const Real *L, Real *Li, Real *M, int w) {
     }
 }
 
+// B <- (the node Q-factors along the root-to-`target` path) applied to
+// B = I at the root (Appendix C.2, downsweep): each node on the path gives its
+// child [B_0; B_1; ...] = (I - V T V^T)[B; 0] = [B - T B; -Y_1 T B; ...].  T, Y
+// and I are upper triangular, so B stays upper triangular and each product
+// costs about w^3/6 multiply-adds.  C, M: w x w scratch.
 template <class Real>
-__global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParamsT<Real> p) {
+__device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real *C, Real *M) {
+    const int w = p.w, tid = threadIdx.x, nthr = blockDim.x;
+    const size_t ww = (size_t)w * w;
+    int anc[41], Nlev[41];
+    int64_t offl[41];
+    anc[0] = target; Nlev[0] = p.P; offl[0] = 0;
+    for (int lv = 0; lv < p.L; ++lv) {
+        anc[lv + 1] = anc[lv] / p.k;
+        Nlev[lv + 1] = (Nlev[lv] + p.k - 1) / p.k;
+        offl[lv + 1] = offl[lv] + Nlev[lv];
+    }
+    for (int idx = tid; idx < w * w; idx += nthr) B[idx] = (idx % w == idx / w) ? Real(1) : Real(0);
+    __syncthreads();
+    for (int lv = p.L - 1; lv >= 0; --lv) {
+        const int parent = anc[lv + 1], first = parent * p.k;
+        const int cnt = min(p.k, Nlev[lv] - first);
+        if (cnt == 1) continue;
+        const int pos = anc[lv] - first;
+        const int64_t pidx = offl[lv + 1] + parent;
+        const Real *Tn = p.wsT + (size_t)pidx * ww;
+        for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tn[idx];
+        __syncthreads();
+        upper_upper(M, B, C, w, Real(1));          // C = T_node B
+        __syncthreads();
+        if (pos == 0) {
+            for (int idx = tid; idx < w * w; idx += nthr) B[idx] -= C[idx];
+        } else {
+            const Real *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos - 1)) * ww;
+            for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Yn[idx];
+            __syncthreads();
+            upper_upper(M, C, B, w, -Real(1));     // B = -Y_pos C
+        }
+        __syncthreads();
+    }
+}
+
+// Z (over M) = T (V1^T B) for a leaf: V1 = the unit lower top w x w block of
+// the leaf's V (entry (l, i), l > i, at V1[l * ld1v + i * ldv]), T upper (in
+// M on entry), B upper; C is w x w scratch.  Z is upper triangular.
+template <class Real>
+__device__ void leaf_z(const Real *V1, int64_t ldv, const Real *B, Real *C, Real *M, int w) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int idx = tid; idx < w * w; idx += nthr) {          // C = V1^T B (upper)
+        const int i = idx % w, c = idx / w;
+        Real s = Real(0);
+        if (i <= c) {
+            s = B[i + c * w];
+            for (int l = i + 1; l <= c; ++l) s = rfma(V1[(size_t)i * ldv + l], B[l + c * w], s);
+        }
+        C[idx] = s;
+    }
+    __syncthreads();
+    Real z2[(kMaxPanel * kMaxPanel + kThreads - 1) / kThreads];   // Z = T C, then over M
+    int q = 0;
+    for (int idx = tid; idx < w * w; idx += nthr, ++q) {
+        const int i = idx % w, c = idx / w;
+        Real s = Real(0);
+        for (int l = i; l <= c; ++l) s = rfma(M[i + l * w], C[l + c * w], s);
+        z2[q] = s;
+    }
+    __syncthreads();
+    q = 0;
+    for (int idx = tid; idx < w * w; idx += nthr, ++q) M[idx] = z2[q];
+    __syncthreads();
+}
+
+// Downsweep and reconstruction in one launch (Appendix C.2).  W = Q [I; 0]
+// row block p is W_p = (I - V_p T_p V_p^T)[B_p; 0] with B_p from the path
+// root -> leaf p.  The top block X of W (leaf 0's top rows) is formed by every
+// CTA from leaf 0's path and the copy of leaf 0's top V block that the
+// upsweep kept, so no CTA waits for another; then, in every CTA:
+//   X + S = L U with S_jj = sgn(X^_jj) added before column j is eliminated;
+//   V rows = W rows U^{-1} for this leaf's rows below the top w;
+// and CTA 0 writes T = U S L^{-T}, V_top = L and R = -S R^(L) (R^(L) at the root).
+template <class Real>
+__global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *smem = reinterpret_cast<Real *>(smem_raw);
     const int w = p.w, ldS = p.ldW, tid = threadIdx.x, nthr = blockDim.x;
     const size_t ww = (size_t)w * w;
-    Real *X = smem;            // w x w: L (strict lower) and U (upper)
-    Real *Tm = X + ww;         // w x w
-    Real *Li = Tm + ww;        // w x w
-    Real *Ms = Li + ww;        // w x w scratch
-    Real *Sg = Ms + ww;        // w signs
-    Real *rU = Sg + w;         // w reciprocals of diag(U)
-    Real *Wb = rU + w;         // ldS x w
+    Real *B = smem;          // w x w: B of the path walked
+    Real *C = B + ww;        // w x w scratch
+    Real *M = C + ww;        // w x w: T, then Z
+    Real *X = M + ww;        // w x w: X, then L (strict lower) and U
+    Real *Li = X + ww;       // w x w: leaf 0's top V block, then L^{-1}
+    Real *Sg = Li + ww;      // w signs
+    Real *rU = Sg + w;       // w reciprocals of diag(U)
+    Real *Vs = rU + w;       // ldS x w: this leaf's rows of V, then of W and V
 
-    for (int idx = tid; idx < w * w; idx += nthr) X[idx] = __ldcg(p.wsX + idx);
+    const int leaf = blockIdx.x;
+    // X = [B_0; 0] top rows - V0 Z0, V0 = leaf 0's unit lower top block
+    walk_path(p, 0, B, C, M);
+    for (int idx = tid; idx < w * w; idx += nthr) {
+        Li[idx] = __ldcg(p.wsX + idx);
+        M[idx] = __ldcg(p.wsT + idx);                        // T of leaf 0
+    }
     __syncthreads();
-    // X + S = L U, S_jj = sgn(X^_jj) added before column j is eliminated.
+    leaf_z(Li, w, B, C, M, w);
+    for (int idx = tid; idx < w * w; idx += nthr) {
+        const int r = idx % w, c = idx / w;
+        Real s = (r <= c) ? M[r + c * w] : Real(0);
+        for (int i = 0; i < min(r, c + 1); ++i) s = rfma(Li[i * w + r], M[i + c * w], s);
+        X[idx] = B[idx] - s;
+    }
+    __syncthreads();
+    // X + S = L U
     for (int j = 0; j < w; ++j) {
         if (tid == 0) {
-            const Real s = X[j + j * w] < Real(0) ? -Real(1) : Real(1);
-            Sg[j] = s;
-            X[j + j * w] += s;
+            const Real sg = X[j + j * w] < Real(0) ? -Real(1) : Real(1);
+            Sg[j] = sg;
+            X[j + j * w] += sg;
         }
         __syncthreads();
         const Real piv = X[j + j * w];
@@ -538,24 +543,54 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParamsT<Real> 
         __syncthreads();
     }
     for (int j = tid; j < w; j += nthr) rU[j] = Real(1) / X[j + j * w];
-
-    const int leaf = blockIdx.x;
     if (leaf == 0) {
         // T = U S L^{-T}: T(i, c) = sum_{l=i}^{c} U(i, l) S_l Li(c, l)
-        unit_lower_inverse(X, Li, Ms, w);
+        unit_lower_inverse(X, Li, C, w);
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int i = idx % w, c = idx / w;
             Real t = Real(0);
             for (int l = i; l <= c; ++l) t = rfma(X[i + l * w] * Sg[l], (l == c) ? Real(1) : Li[c + l * w], t);
-            Tm[idx] = t;
+            p.Tout[i + c * p.ldt] = t;
         }
-        __syncthreads();
-        for (int idx = tid; idx < w * w; idx += nthr) {
-            const int i = idx % w, c = idx / w;
-            p.Tout[i + c * p.ldt] = Tm[idx];
+    } else {
+        walk_path(p, leaf, B, C, M);                         // leaf 0 keeps B_0
+    }
+    __syncthreads();
+
+    // this leaf: W_p = (I - V_p T_p V_p^T)[B_p; 0], then V rows = W rows U^{-1}
+    const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
+    const int h = (int)(r1 - r0);
+    for (int c = 0; c < w; ++c)
+        for (int r = tid; r < h; r += nthr) Vs[(size_t)c * ldS + r] = p.A[(r0 + r) + c * p.lda];
+    {
+        const Real *Tp = p.wsT + (size_t)leaf * ww;
+        for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tp[idx];
+    }
+    __syncthreads();
+    leaf_z(Vs, ldS, B, C, M, w);
+    for (int r = tid; r < h; r += nthr) {
+        if (r0 + r < w) continue;                           // leaf 0's top block: L \ R below
+        // W(r, c) = [B; 0](r, c) - sum_{i <= min(r, c)} Vhat(r, i) Z(i, c), in place, c descending
+        for (int c = w - 1; c >= 0; --c) {
+            Real s = (r <= c) ? M[r + c * w] : Real(0);
+            const int iend = min(r, c + 1);
+            for (int i = 0; i < iend; ++i) s = rfma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
+            Vs[(size_t)c * ldS + r] = ((r < w) ? B[r + c * w] : Real(0)) - s;
         }
-        // top block of the panel: L strictly below the diagonal, R = -S R^(L)
-        // on and above it; R^(L) sits in the last node slot (the root).
+        // V(r, :) U = W(r, :), in place, j ascending
+        for (int j = 0; j < w; ++j) {
+            Real v = Vs[(size_t)j * ldS + r];
+            for (int l = 0; l < j; ++l) v = rfma(-Vs[(size_t)l * ldS + r], X[l + j * w], v);
+            Vs[(size_t)j * ldS + r] = v * rU[j];
+        }
+    }
+    __syncthreads();
+    for (int c = 0; c < w; ++c)
+        for (int r = tid; r < h; r += nthr)
+            if (r0 + r >= w) p.A[(r0 + r) + c * p.lda] = Vs[(size_t)c * ldS + r];
+    if (leaf == 0) {
+        // top block: L strictly below the diagonal, R = -S R^(L) on and above;
+        // R^(L) sits in the last node slot (the root)
         int64_t nodes = p.P, Nl = p.P;
         while (Nl > 1) { Nl = (Nl + p.k - 1) / p.k; nodes += Nl; }
         const Real *RL = p.wsR + (size_t)(nodes - 1) * ww;
@@ -564,30 +599,10 @@ __global__ void __launch_bounds__(kThreads) tsqr_recon_kernel(TsqrParamsT<Real> 
             p.A[i + c * p.lda] = (i <= c) ? -Sg[i] * __ldcg(RL + idx) : X[i + c * w];
         }
     }
-    __syncthreads();
-
-    // V rows: V(r, :) = W(r, :) U^{-1} for the rows of this leaf below the top w.
-    const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
-    const int64_t rs = max(r0, (int64_t)w);
-    const int h = (int)max((int64_t)0, r1 - rs);
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < h; r += nthr) Wb[(size_t)c * ldS + r] = p.A[(rs + r) + c * p.lda];
-    __syncthreads();
-    for (int r = tid; r < h; r += nthr) {
-        for (int j = 0; j < w; ++j) {
-            Real v = Wb[(size_t)j * ldS + r];
-            for (int l = 0; l < j; ++l) v = rfma(-Wb[(size_t)l * ldS + r], X[l + j * w], v);
-            Wb[(size_t)j * ldS + r] = v * rU[j];
-        }
-    }
-    __syncthreads();
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < h; r += nthr) p.A[(rs + r) + c * p.lda] = Wb[(size_t)c * ldS + r];
 }
 
 size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + w); }
-size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 3 * (size_t)w * w); }
-size_t recon_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 4 * (size_t)w * w + 2 * w); }
+size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 5 * (size_t)w * w + 2 * w); }
 
 constexpr size_t kSmemCap = 200 * 1024;
 constexpr int kDefaultFanout = 8;
@@ -606,8 +621,7 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     // tallest leaf that every kernel's shared memory can hold
     const size_t cap_el = kSmemCap / sizeof(double);
     int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + w)) / w);                      // up
-    hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 3 * (size_t)w * w) / w));           // down
-    hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 4 * (size_t)w * w - 2 * w) / w));   // recon
+    hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 5 * (size_t)w * w - 2 * w) / w));   // down + recon
     if (hcap < w) return false;
     // default: about one leaf per SM (the leaf phase is the only one that
     // uses the whole GPU), but at least 128 rows - shorter panels then get
@@ -639,8 +653,7 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     pl.ncount = (size_t)std::max<int64_t>(internal, 1);
     pl.smem_up = up_smem(pl.ldS, w);
     pl.smem_down = down_smem(pl.ldW, w);
-    pl.smem_recon = recon_smem(pl.ldW, w);
-    if (pl.smem_up > kSmemCap || pl.smem_down > kSmemCap || pl.smem_recon > kSmemCap) return false;
+    if (pl.smem_up > kSmemCap || pl.smem_down > kSmemCap) return false;
     *plan = pl;
     return true;
 }
@@ -685,8 +698,7 @@ gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, Real *A, int64_t lda,
     if (!(ex.device >= 0 && ex.device < 64) || !attr_done[ex.device].load(std::memory_order_acquire)) {
         const int cap = (int)kSmemCap;
         if (cudaFuncSetAttribute(tsqr_up_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
-            cudaFuncSetAttribute(tsqr_down_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
-            cudaFuncSetAttribute(tsqr_recon_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
+            cudaFuncSetAttribute(tsqr_down_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess)
             return GBQR_ECUDA;
         if (ex.device >= 0 && ex.device < 64) attr_done[ex.device].store(true, std::memory_order_release);
     }
@@ -703,14 +715,11 @@ gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, Real *A, int64_t lda,
 
     trace_begin(ex, FAM_TSQR_DOWN);
     tsqr_down_kernel<Real><<<pl.P, kThreads, pl.smem_down, ex.stream>>>(p);
-    st = trace_end(ex, FAM_TSQR_DOWN, 2.0 * mp * ww + (double)pl.P * (2.0 * pl.L + 2.0) * ww * w,
+    // per leaf: two path walks (~2 L products of w^3/6 each), X and its LU
+    // (w^3/3), the leaf's W (~m_p w^2) and V = W U^{-1} (~m_p w^2 / 2)
+    st = trace_end(ex, FAM_TSQR_DOWN,
+                   3.0 * mp * ww + (double)pl.P * ((4.0 * pl.L + 2.0) * ww * w / 3.0 + 2.0 * ww * w / 3.0),
                    (double)sizeof(Real) * (2.0 * mp * w + 2.0 * (double)pl.nodes * ww));
-    if (st != GBQR_OK) return st;
-
-    trace_begin(ex, FAM_TSQR_RECON);
-    tsqr_recon_kernel<Real><<<pl.P, kThreads, pl.smem_recon, ex.stream>>>(p);
-    st = trace_end(ex, FAM_TSQR_RECON, mp * ww + (double)pl.P * ww * w * 2.0 / 3.0,
-                   (double)sizeof(Real) * (2.0 * mp * w + 2.0 * ww));
     return st;
 }
 
