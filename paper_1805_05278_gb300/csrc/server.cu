@@ -43,10 +43,10 @@ struct Record {
 
 // GBQR_PREC_AUTO: the tensor-core updates only pay off where the update
 // GEMMs dominate the solve.  Measured single-solve speed-ups of the mixed
-// path over FP64 (graded columns, kappa ~ 1e4): 2.44x at 65536 x 1024, 1.62x
-// at 65536 x 512, 1.19x at 16384 x 512, 1.17x at 65536 x 256, 1.04x at
-// 4096 x 1024 (all m n^2 >= 4e9), even at 16384 x 256, slower below (the FP64
-// panel chain dominates and the refinement adds its GMRES steps).
+// path over FP64 (graded columns, kappa ~ 1e4): 2.71x at 65536 x 1024, 1.76x
+// at 65536 x 512, 1.24x at 16384 x 512, 1.23x at 65536 x 256, 1.05x at
+// 4096 x 1024 (all m n^2 >= 4e9), 1.04x at 16384 x 256, slower below (the
+// FP64 panel chain dominates and the refinement adds its GMRES steps).
 int auto_precision(int64_t m, int64_t n) {
     return (n >= 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
 }
