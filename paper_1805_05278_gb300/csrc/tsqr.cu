@@ -100,22 +100,35 @@ struct LeafRows {
 };
 
 // Rows of column j below its pivot in cnt stacked w x w upper triangles:
-// rows 0..j of every triangle after the first.
+// rows 0..j of every triangle after the first.  The (cnt-1)(j+1) entries are
+// spread over the lanes as one flat list, so a lane touches about
+// (cnt-1)(j+1)/32 of them instead of cnt-1.  Entry e = b d + r (d = j+1) is
+// row r of triangle b+1; a lane steps e by 32 = q d + s, so (b, r) advances
+// by (q, s) with at most one carry and only the first entry needs a division.
 struct MergeRows {
     int w, cnt;
     template <class F>
-    __device__ __forceinline__ void each(int j, int lane, F &&f) const {
-        for (int i = 1; i < cnt; ++i)
-            for (int r = lane; r <= j; r += 32) f(i * w + r);
+    __device__ __forceinline__ void walk(int d, int e, F &&f) const {
+        const int n = (cnt - 1) * d;
+        if (e >= n) return;
+        const int q = 32 / d, s = 32 - q * d;
+        int b = e / d, r = e - b * d;
+        for (; e < n; e += 32) {
+            f((b + 1) * w + r);
+            b += q;
+            r += s;
+            if (r >= d) { r -= d; ++b; }
+        }
     }
     template <class F>
+    __device__ __forceinline__ void each(int j, int lane, F &&f) const {
+        walk(j + 1, lane, f);
+    }
+    // entry 0 of the flat list is the pivot; entry i > 0 is e = i - 1 above
+    template <class F>
     __device__ __forceinline__ void each_with_pivot(int j, int lane, F &&f) const {
-        const int n = 1 + (cnt - 1) * (j + 1);
-        for (int idx = lane; idx < n; idx += 32) {
-            if (idx == 0) { f(j, true); continue; }
-            const int b = (idx - 1) / (j + 1);
-            f((b + 1) * w + (idx - 1 - b * (j + 1)), false);
-        }
+        if (lane == 0) f(j, true);
+        walk(j + 1, lane == 0 ? 31 : lane - 1, [&](int r) { f(r, false); });
     }
 };
 
