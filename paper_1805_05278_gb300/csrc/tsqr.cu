@@ -37,6 +37,11 @@ __device__ __forceinline__ double rfma(double a, double b, double c) { return fm
 __device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double real_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float real_sqrt(float x) { return sqrtf(x); }
+// 1/x rounded to nearest: the same value as the IEEE division 1/x, through
+// the reciprocal intrinsic, which takes about 60 % of the division's FP64
+// issue slots on this part
+__device__ __forceinline__ double real_rcp(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float real_rcp(float x) { return __frcp_rn(x); }
 
 template <class Real>
 struct TsqrParamsT {
@@ -91,6 +96,11 @@ struct LeafRows {
     __device__ __forceinline__ void each(int j, int lane, F &&f) const {
         for (int r = j + 1 + lane; r < h; r += 32) f(r);
     }
+    // Of the rows step j touches, those below the pivot of column j+1; no
+    // row of column j+1 below its pivot is outside step j's rows.
+    __device__ __forceinline__ bool below_next(int j, int r) const { return r > j + 1; }
+    template <class F>
+    __device__ __forceinline__ void each_untouched(int, int, F &&) const {}
     // pivot row j first (f(r, true)), then rows(j): one pass, no separate
     // pivot-row term
     template <class F>
@@ -107,6 +117,14 @@ struct LeafRows {
 // by (q, s) with at most one carry and only the first entry needs a division.
 struct MergeRows {
     int w, cnt;
+    // Of the rows step j touches, those below the pivot of column j+1 (every
+    // triangle after the first); row j+1 of those triangles is below that
+    // pivot too but outside step j's rows.
+    __device__ __forceinline__ bool below_next(int, int r) const { return r >= w; }
+    template <class F>
+    __device__ __forceinline__ void each_untouched(int j, int lane, F &&f) const {
+        for (int i = 1 + lane; i < cnt; i += 32) f(i * w + j + 1);
+    }
     template <class F>
     __device__ __forceinline__ void walk(int d, int e, F &&f) const {
         const int n = (cnt - 1) * d;
@@ -139,19 +157,16 @@ struct MergeRows {
 // q = 1 / (beta d): scale = 1/d = beta q and tau = (beta - alpha)/beta = -d^2 q,
 // so the pivot costs one square root and one reciprocal.
 template <class Real, class Rows>
-__device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau) {
+__device__ __forceinline__ void finish_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau, Real sig2) {
     const int lane = threadIdx.x & 31;
     Real *col = S + (size_t)c * ldS;
-    Real part = Real(0);
-    rows.each(c, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
-    const Real sig2 = warp_sum(part);
     const Real alpha = col[c];
     const Real nrm = real_sqrt(rfma(alpha, alpha, sig2));
     const Real beta = alpha < Real(0) ? nrm : -nrm;
     Real tj = Real(2);
     if (beta != Real(0)) {
         const Real d = alpha - beta;
-        const Real q = Real(1) / (beta * d);
+        const Real q = real_rcp(beta * d);
         const Real scal = beta * q;
         tj = -(d * d) * q;
         rows.each(c, lane, [&](int r) { col[r] *= scal; });
@@ -159,6 +174,39 @@ __device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau)
     __syncwarp();
     if (lane == 0) { col[c] = beta; tau[c] = tj; }
     __syncwarp();
+}
+
+template <class Real, class Rows>
+__device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau) {
+    const int lane = threadIdx.x & 31;
+    const Real *col = S + (size_t)c * ldS;
+    Real part = Real(0);
+    rows.each(c, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
+    finish_pivot(S, ldS, c, rows, tau, warp_sum(part));
+}
+
+// The pivot warp's share of step j: reflector j applied to column c = j+1
+// (as warp_apply does), with the squared norm of column c below its pivot
+// summed in the same pass over the rows, then column c turned into
+// reflector c.  One pass over the column instead of two.
+template <class Real, class Rows>
+__device__ void pivot_next(Real *S, int ldS, int j, const Rows &rows, Real tj, Real *tau) {
+    const int lane = threadIdx.x & 31, c = j + 1;
+    const Real *vj = S + (size_t)j * ldS;
+    Real *col = S + (size_t)c * ldS;
+    Real acc = Real(0);
+    rows.each_with_pivot(j, lane, [&](int r, bool piv) { acc = rfma(piv ? Real(1) : vj[r], col[r], acc); });
+    const Real f = tj * warp_sum(acc);
+    Real part = Real(0);
+    rows.each_with_pivot(j, lane, [&](int r, bool piv) {
+        const Real x = rfma(-f, piv ? Real(1) : vj[r], col[r]);
+        col[r] = x;
+        if (rows.below_next(j, r)) part = rfma(x, x, part);
+    });
+    rows.each_untouched(j, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
+    const Real sig2 = warp_sum(part);
+    __syncwarp();
+    finish_pivot(S, ldS, c, rows, tau, sig2);
 }
 
 // One warp applies reflector j to N columns (c > j: A(:,c) -= tau_j v_j (v_j^T A(:,c)))
@@ -212,12 +260,7 @@ __device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, Rea
         const int nxt = j + 1;
         const int pw = j % nw;                         // pivot warp of this step
         if (wid == pw) {
-            if (nxt < w) {
-                const int one[4] = {nxt, 0, 0, 0};
-                warp_apply<1>(S, ldS, j, rows, one, tj, G, w);
-                __syncwarp();
-                warp_pivot(S, ldS, nxt, rows, tau);
-            }
+            if (nxt < w) pivot_next(S, ldS, j, rows, tj, tau);
         } else if (nw < 8 || wid != (pw + 4) % nw) {
             // every other column (not j, not j+1) to the other warps, round
             // robin - except the warp that shares the pivot warp's SM
@@ -555,7 +598,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
         }
         __syncthreads();
     }
-    for (int j = tid; j < w; j += nthr) rU[j] = Real(1) / X[j + j * w];
+    for (int j = tid; j < w; j += nthr) rU[j] = real_rcp(X[j + j * w]);
     if (leaf == 0) {
         // T = U S L^{-T}: T(i, c) = sum_{l=i}^{c} U(i, l) S_l Li(c, l)
         unit_lower_inverse(X, Li, C, w);
