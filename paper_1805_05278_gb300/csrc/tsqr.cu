@@ -87,6 +87,60 @@ __device__ __forceinline__ void warp_sum_n(Real (&v)[4]) {
     v[3] = __shfl_sync(kFull, k, 24);
 }
 
+// dst(r, c) = src(r, c) for an h x w column-major block (dst ld ldd, src ld
+// lds), the whole CTA: every thread issues up to 8 loads before its first
+// store, so a block read from L2 or HBM costs about one memory latency
+// instead of one per column.
+template <class Real>
+__device__ __forceinline__ void load_block(Real *dst, int64_t ldd, const Real *src, int64_t lds, int h, int w) {
+    constexpr int kBatch = 8;
+    const int tid = threadIdx.x, nthr = blockDim.x, total = h * w;
+    for (int base = tid; base < total; base += kBatch * nthr) {
+        Real v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int idx = base + k * nthr;
+            if (idx < total) {
+                const int c = idx / h, r = idx - c * h;
+                v[k] = __ldcg(src + r + (int64_t)c * lds);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int idx = base + k * nthr;
+            if (idx < total) {
+                const int c = idx / h, r = idx - c * h;
+                dst[r + (int64_t)c * ldd] = v[k];
+            }
+        }
+    }
+}
+
+// The cnt consecutive w x w slots at src (slot i, entry (row, col) at
+// i w^2 + row + col w) stacked into S: slot i's entry goes to S(i w + row,
+// col).  Up to 8 loads in flight per thread, as in load_block.
+template <class Real>
+__device__ __forceinline__ void load_stack(Real *S, int64_t ldS, const Real *src, int cnt, int w) {
+    constexpr int kBatch = 8;
+    const int tid = threadIdx.x, nthr = blockDim.x, ww = w * w, total = cnt * ww;
+    for (int base = tid; base < total; base += kBatch * nthr) {
+        Real v[kBatch];
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int e = base + k * nthr;
+            if (e < total) v[k] = __ldcg(src + e);
+        }
+#pragma unroll
+        for (int k = 0; k < kBatch; ++k) {
+            const int e = base + k * nthr;
+            if (e < total) {
+                const int i = e / ww, rem = e - i * ww, col = rem / w, row = rem - col * w;
+                S[(i * w + row) + (int64_t)col * ldS] = v[k];
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ int64_t leaf_begin(int64_t mp, int P, int p) { return (int64_t)p * mp / P; }
 
 // Rows of column j below its pivot in a leaf block: j+1 .. h-1.
@@ -341,8 +395,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
     const int h = (int)(r1 - r0);
     const size_t ww = (size_t)w * w;
 
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < h; r += nthr) S[(size_t)c * ldS + r] = p.A[(r0 + r) + c * p.lda];
+    load_block(S, ldS, p.A + r0, p.lda, h, w);
     __syncthreads();
     householder_block(S, ldS, w, LeafRows{h}, tau, G);
 
@@ -390,11 +443,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
             if (!s_last) return;
             __threadfence();
             if (tid == 0) p.counters[pidx - p.P] = 0u;
-            for (int i = 0; i < cnt; ++i) {
-                const Real *Rc = p.wsR + (size_t)(off + first + i) * ww;
-                for (int idx = tid; idx < w * w; idx += nthr)
-                    S[(size_t)(idx / w) * ldS + i * w + (idx % w)] = __ldcg(Rc + idx);
-            }
+            load_stack(S, ldS, p.wsR + (size_t)(off + first) * ww, cnt, w);   // the children's R, stacked
             __syncthreads();
             householder_block(S, ldS, w, MergeRows{w, cnt}, tau, G);
             Real *Rn = p.wsR + (size_t)pidx * ww, *Tn = p.wsT + (size_t)pidx * ww;
@@ -475,9 +524,10 @@ __device__ void unit_lower_inverse(const Real *L, Real *Li, Real *M, int w) {
 // and I are upper triangular, so B stays upper triangular and each product
 // costs about w^3/6 multiply-adds.  C, M: w x w scratch.
 template <class Real>
-__device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real *C, Real *M) {
+__device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real *C, Real *M, Real *Yb) {
     const int w = p.w, tid = threadIdx.x, nthr = blockDim.x;
-    const size_t ww = (size_t)w * w;
+    const int ww = w * w;
+    constexpr int kPer = (kMaxPanel * kMaxPanel + kThreads - 1) / kThreads;   // entries per thread
     int anc[41], Nlev[41];
     int64_t offl[41];
     anc[0] = target; Nlev[0] = p.P; offl[0] = 0;
@@ -486,28 +536,55 @@ __device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real 
         Nlev[lv + 1] = (Nlev[lv] + p.k - 1) / p.k;
         offl[lv + 1] = offl[lv] + Nlev[lv];
     }
-    for (int idx = tid; idx < w * w; idx += nthr) B[idx] = (idx % w == idx / w) ? Real(1) : Real(0);
-    __syncthreads();
-    for (int lv = p.L - 1; lv >= 0; --lv) {
-        const int parent = anc[lv + 1], first = parent * p.k;
-        const int cnt = min(p.k, Nlev[lv] - first);
-        if (cnt == 1) continue;
-        const int pos = anc[lv] - first;
+    // the node above level lv merges cnt children; a single child passes through
+    auto count = [&](int lv) { return min(p.k, Nlev[lv] - anc[lv + 1] * p.k); };
+    auto next_merge = [&](int lv) {
+        while (lv >= 0 && count(lv) == 1) --lv;
+        return lv;
+    };
+    // the node's T and (for a child after the first) its Y block, staged in
+    // registers so that the next level's loads overlap this level's products
+    Real tn[kPer], yn[kPer];
+    auto fetch = [&](int lv) {
+        const int parent = anc[lv + 1], pos = anc[lv] - parent * p.k;
         const int64_t pidx = offl[lv + 1] + parent;
         const Real *Tn = p.wsT + (size_t)pidx * ww;
-        for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tn[idx];
+        const Real *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos > 0 ? pos - 1 : 0)) * ww;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = tid + q * nthr;
+            if (idx < ww) {
+                tn[q] = __ldcg(Tn + idx);
+                if (pos > 0) yn[q] = __ldcg(Yn + idx);
+            }
+        }
+    };
+    for (int idx = tid; idx < ww; idx += nthr) B[idx] = (idx % w == idx / w) ? Real(1) : Real(0);
+    int cur = next_merge(p.L - 1);
+    if (cur >= 0) fetch(cur);
+    __syncthreads();
+    while (cur >= 0) {
+        const int pos = anc[cur] - anc[cur + 1] * p.k;
+#pragma unroll
+        for (int q = 0; q < kPer; ++q) {
+            const int idx = tid + q * nthr;
+            if (idx < ww) {
+                M[idx] = tn[q];
+                if (pos > 0) Yb[idx] = yn[q];
+            }
+        }
         __syncthreads();
+        const int nxt = next_merge(cur - 1);
+        if (nxt >= 0) fetch(nxt);
         upper_upper(M, B, C, w, Real(1));          // C = T_node B
         __syncthreads();
         if (pos == 0) {
-            for (int idx = tid; idx < w * w; idx += nthr) B[idx] -= C[idx];
+            for (int idx = tid; idx < ww; idx += nthr) B[idx] -= C[idx];
         } else {
-            const Real *Yn = p.wsY + ((size_t)(pidx - p.P) * (p.k - 1) + (pos - 1)) * ww;
-            for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Yn[idx];
-            __syncthreads();
-            upper_upper(M, C, B, w, -Real(1));     // B = -Y_pos C
+            upper_upper(Yb, C, B, w, -Real(1));    // B = -Y_pos C
         }
         __syncthreads();
+        cur = nxt;
     }
 }
 
@@ -566,7 +643,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
 
     const int leaf = blockIdx.x;
     // X = [B_0; 0] top rows - V0 Z0, V0 = leaf 0's unit lower top block
-    walk_path(p, 0, B, C, M);
+    walk_path(p, 0, B, C, M, X);                          // X is free until formed below
     for (int idx = tid; idx < w * w; idx += nthr) {
         Li[idx] = __ldcg(p.wsX + idx);
         M[idx] = __ldcg(p.wsT + idx);                        // T of leaf 0
@@ -609,15 +686,14 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
             p.Tout[i + c * p.ldt] = t;
         }
     } else {
-        walk_path(p, leaf, B, C, M);                         // leaf 0 keeps B_0
+        walk_path(p, leaf, B, C, M, Li);                     // leaf 0 keeps B_0; Li is free here
     }
     __syncthreads();
 
     // this leaf: W_p = (I - V_p T_p V_p^T)[B_p; 0], then V rows = W rows U^{-1}
     const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
     const int h = (int)(r1 - r0);
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < h; r += nthr) Vs[(size_t)c * ldS + r] = p.A[(r0 + r) + c * p.lda];
+    load_block(Vs, ldS, p.A + r0, p.lda, h, w);
     {
         const Real *Tp = p.wsT + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) M[idx] = Tp[idx];
