@@ -204,76 +204,111 @@ struct MergeRows {
     }
 };
 
-// One warp turns column c into a Householder reflector: beta on the pivot,
-// the scaled vector below it, tau[c].  beta = -sgn(alpha) ||column||,
-// sgn(0) = +1, no exception for a reduced column (tau = 2); a zero column
-// gives v = e_c, tau = 2.  With d = alpha - beta (no cancellation) and
-// q = 1 / (beta d): scale = 1/d = beta q and tau = (beta - alpha)/beta = -d^2 q,
-// so the pivot costs one square root and one reciprocal.
-template <class Real, class Rows>
-__device__ __forceinline__ void finish_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau, Real sig2) {
+// Reflectors are kept unnormalised while a block is factored.  With
+// beta = -sgn(alpha) ||column|| (sgn(0) = +1), d = alpha - beta (no
+// cancellation) and x the column below its pivot, the normalised vector is
+// v = [1; x/d] and tau = (beta - alpha)/beta; with vh = [d; x] and
+// q = 1/(beta d) the same reflector is H = I - tau v v^T = I + q vh vh^T.
+// So the pivot warp only publishes beta (on the pivot), d and beta*d: the
+// reciprocal q is taken by the next step's pivot warp, overlapped with its
+// dot products, and the scaling of x by 1/d, tau and the Gram entries are
+// settled once per block (finish_block).  A zero column (beta = 0) is stored
+// as d = 1, beta*d = 0, and q_of maps it to q = -2: H = I - 2 e e^T, tau = 2.
+template <class Real>
+struct Refl {
+    Real *tau;   // tau[c], from finish_block on
+    Real *d;     // d[c]
+    Real *bd;    // beta[c] * d[c]  (0 for a zero column)
+    Real *q;     // q[c] = 1/(beta d), published in step c
+    Real *sc;    // 1/d[c], from finish_block on
+};
+
+template <class Real>
+__device__ __forceinline__ Real q_of(Real bd) { return bd == Real(0) ? Real(-2) : real_rcp(bd); }
+
+// Named barrier 1 hands q_j from the pivot warp (bar.arrive) to the six warps
+// that update other columns (bar.sync): 7 warps, 224 threads.  Every step the
+// pivot warp arrives exactly once and each of those six warps syncs exactly
+// once; the eighth warp (the pivot warp's sub-partition partner) takes no part.
+constexpr int kQBarrier = 1;
+constexpr int kQThreads = 7 * 32;
+// (barrier.* without .aligned: correct even where a warp is not converged)
+__device__ __forceinline__ void q_arrive() {
+    __syncwarp();
+    asm volatile("barrier.arrive %0, %1;" ::"n"(kQBarrier), "n"(kQThreads) : "memory");
+}
+__device__ __forceinline__ void q_sync() {
+    __syncwarp();
+    asm volatile("barrier.sync %0, %1;" ::"n"(kQBarrier), "n"(kQThreads) : "memory");
+}
+
+// One warp turns column c (squared norm below its pivot sig2) into an
+// unnormalised reflector: beta on the pivot, d and beta*d published.
+template <class Real>
+__device__ __forceinline__ void publish_pivot(Real *S, int ldS, int c, const Refl<Real> &rf, Real sig2) {
     const int lane = threadIdx.x & 31;
     Real *col = S + (size_t)c * ldS;
     const Real alpha = col[c];
     const Real nrm = real_sqrt(rfma(alpha, alpha, sig2));
     const Real beta = alpha < Real(0) ? nrm : -nrm;
-    Real tj = Real(2);
-    if (beta != Real(0)) {
-        const Real d = alpha - beta;
-        const Real q = real_rcp(beta * d);
-        const Real scal = beta * q;
-        tj = -(d * d) * q;
-        rows.each(c, lane, [&](int r) { col[r] *= scal; });
-    }
+    const Real d = beta != Real(0) ? alpha - beta : Real(1);
     __syncwarp();
-    if (lane == 0) { col[c] = beta; tau[c] = tj; }
+    if (lane == 0) { col[c] = beta; rf.d[c] = d; rf.bd[c] = beta * d; }
     __syncwarp();
 }
 
 template <class Real, class Rows>
-__device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, Real *tau) {
+__device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, const Refl<Real> &rf) {
     const int lane = threadIdx.x & 31;
     const Real *col = S + (size_t)c * ldS;
     Real part = Real(0);
     rows.each(c, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
-    finish_pivot(S, ldS, c, rows, tau, warp_sum(part));
+    publish_pivot(S, ldS, c, rf, warp_sum(part));
 }
 
-// The pivot warp's share of step j: reflector j applied to column c = j+1
-// (as warp_apply does), with the squared norm of column c below its pivot
-// summed in the same pass over the rows, then column c turned into
-// reflector c.  One pass over the column instead of two.
+// The pivot warp's share of step j: q_j for the other warps (named barrier),
+// then reflector j applied to column c = j+1 with the squared norm of column c
+// below its pivot summed in the same pass, then column c published.
 template <class Real, class Rows>
-__device__ void pivot_next(Real *S, int ldS, int j, const Rows &rows, Real tj, Real *tau) {
+__device__ void pivot_step(Real *S, int ldS, int j, int w, const Rows &rows, const Refl<Real> &rf) {
     const int lane = threadIdx.x & 31, c = j + 1;
+    const Real dj = rf.d[j];
+    const Real qj = q_of(rf.bd[j]);
+    if (lane == 0) rf.q[j] = qj;
+    __syncwarp();
+    __threadfence_block();
+    q_arrive();
+    if (c >= w) return;
     const Real *vj = S + (size_t)j * ldS;
     Real *col = S + (size_t)c * ldS;
     Real acc = Real(0);
-    rows.each_with_pivot(j, lane, [&](int r, bool piv) { acc = rfma(piv ? Real(1) : vj[r], col[r], acc); });
-    const Real f = tj * warp_sum(acc);
+    rows.each_with_pivot(j, lane, [&](int r, bool piv) { acc = rfma(piv ? dj : vj[r], col[r], acc); });
+    const Real f = qj * warp_sum(acc);
     Real part = Real(0);
     rows.each_with_pivot(j, lane, [&](int r, bool piv) {
-        const Real x = rfma(-f, piv ? Real(1) : vj[r], col[r]);
+        const Real x = rfma(f, piv ? dj : vj[r], col[r]);
         col[r] = x;
         if (rows.below_next(j, r)) part = rfma(x, x, part);
     });
     rows.each_untouched(j, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
     const Real sig2 = warp_sum(part);
     __syncwarp();
-    finish_pivot(S, ldS, c, rows, tau, sig2);
+    publish_pivot(S, ldS, c, rf, sig2);
 }
 
-// One warp applies reflector j to N columns (c > j: A(:,c) -= tau_j v_j (v_j^T A(:,c)))
-// or, for c < j, records the Gram entry G(c, j) = v_c^T v_j: both need the
-// same inner product s_c = A(j, c) + sum_r v_j(r) A(r, c).
+// One warp applies reflector j to N columns (c > j: A(:,c) += q_j vh_j
+// (vh_j^T A(:,c))) or, for c < j, records the unscaled Gram entry
+// vh_c^T vh_j (scaled to v_c^T v_j by finish_block).  q_j is taken from the
+// pivot warp through the named barrier, once per step (*synced).
 template <int N, class Real, class Rows>
 __device__ __forceinline__ void warp_apply(Real *S, int ldS, int j, const Rows &rows, const int (&cols)[4],
-                                           Real tj, Real *G, int w) {
+                                           const Refl<Real> &rf, Real *G, int w, bool *synced, Real *qj) {
     const int lane = threadIdx.x & 31;
     const Real *vj = S + (size_t)j * ldS;
+    const Real dj = rf.d[j];
     Real acc[4] = {Real(0), Real(0), Real(0), Real(0)};
     rows.each_with_pivot(j, lane, [&](int r, bool piv) {
-        const Real v = piv ? Real(1) : vj[r];
+        const Real v = piv ? dj : vj[r];
 #pragma unroll
         for (int q = 0; q < N; ++q) acc[q] = rfma(v, S[r + (size_t)cols[q] * ldS], acc[q]);
     });
@@ -282,10 +317,11 @@ __device__ __forceinline__ void warp_apply(Real *S, int ldS, int j, const Rows &
     for (int q = 0; q < N; ++q) {
         const int c = cols[q];
         if (c > j) {
-            const Real f = tj * acc[q];
+            if (!*synced) { q_sync(); *synced = true; *qj = rf.q[j]; }
+            const Real f = *qj * acc[q];
             Real *colc = S + (size_t)c * ldS;
             rows.each_with_pivot(j, lane, [&](int r, bool piv) {
-                colc[r] = rfma(-f, piv ? Real(1) : vj[r], colc[r]);
+                colc[r] = rfma(f, piv ? dj : vj[r], colc[r]);
             });
         } else if (lane == 0) {
             G[c + j * w] = acc[q];
@@ -295,50 +331,70 @@ __device__ __forceinline__ void warp_apply(Real *S, int ldS, int j, const Rows &
 
 // Householder QR of the w columns held in shared memory S (column-major,
 // leading dimension ldS); column j acts on its pivot row j and the rows that
-// `rows` lists.  During step j one warp (j % nw) updates column j+1 and turns
-// it into the next reflector while the other warps share every remaining
-// column round robin, so each step needs a single barrier.  On GB300 a warp
-// issues at most one FP64 instruction per ~64 cycles and an SM sub-partition
-// one per ~76, so the step time is the FP64 instruction count of the busiest
-// warp / sub-partition: the pivot warp (square root, reciprocal, one warp
-// reduction) carries nothing else.  On return: R on and above the pivots, the vectors below them
-// (unit pivot implied), tau[0:w], and the strict upper Gram matrix
-// G(c, j) = v_c^T v_j (ld w) from which the kernel T is built.
+// `rows` lists.  During step j one warp (j % 8) updates column j+1 and turns
+// it into the next reflector while six others share every remaining column
+// round robin, so each step needs one CTA barrier (and the q_j hand-over).
+// On GB300 a warp issues at most one FP64 instruction per ~64 cycles and an
+// SM sub-partition one per ~76, so the step time is the FP64 instruction
+// count of the busiest warp / sub-partition: the pivot warp (square root,
+// two warp reductions) carries nothing else, and the warp that shares its
+// sub-partition (warp i runs on sub-partition i % 4) gets no columns.
+// Leaves the reflectors unnormalised (vh_c below the pivots, d, beta*d, q);
+// finish_block settles them.
 template <class Real, class Rows>
-__device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, Real *tau, Real *G) {
-    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (wid == 0) warp_pivot(S, ldS, 0, rows, tau);
+__device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, const Refl<Real> &rf, Real *G) {
+    static_assert(kThreads == 256, "the q_j hand-over is laid out for 8 warps");
+    constexpr int nw = kThreads / 32;
+    const int wid = threadIdx.x >> 5;
+    if (wid == 0) warp_pivot(S, ldS, 0, rows, rf);
     __syncthreads();
     for (int j = 0; j < w; ++j) {
-        const Real tj = tau[j];
         const int nxt = j + 1;
         const int pw = j % nw;                         // pivot warp of this step
+        const int partner = (pw + 4) % nw;
         if (wid == pw) {
-            if (nxt < w) pivot_next(S, ldS, j, rows, tj, tau);
-        } else if (nw < 8 || wid != (pw + 4) % nw) {
-            // every other column (not j, not j+1) to the other warps, round
-            // robin - except the warp that shares the pivot warp's SM
-            // sub-partition (warp i runs on sub-partition i % 4): the pivot
-            // chain is bound by its FP64 issue slots, and a worker beside it
-            // would take them
+            pivot_step(S, ldS, j, w, rows, rf);
+        } else if (wid != partner) {
             const int nexcl = (nxt < w) ? 2 : 1;
             const int ncols = w - nexcl;
-            const int partner = (nw >= 8) ? (pw + 4) % nw : -1;
-            const int nwork = (nw >= 8) ? nw - 2 : nw - 1;
+            constexpr int nwork = nw - 2;
             int me = (wid - pw - 1 + nw) % nw;        // 0 .. nw-2
-            if (partner >= 0 && me > (partner - pw - 1 + nw) % nw) --me;   // skip the partner's slot
+            if (me > (partner - pw - 1 + nw) % nw) --me;   // skip the partner's slot
+            bool synced = false;
+            Real qj = Real(0);
             int cols[4] = {0, 0, 0, 0};
             int g = 0;
             for (int t = me; t < ncols; t += nwork) {
                 cols[g++] = (t < j) ? t : t + nexcl;
-                if (g == 4) { warp_apply<4>(S, ldS, j, rows, cols, tj, G, w); g = 0; }
+                if (g == 4) { warp_apply<4>(S, ldS, j, rows, cols, rf, G, w, &synced, &qj); g = 0; }
             }
-            if (g == 1) warp_apply<1>(S, ldS, j, rows, cols, tj, G, w);
-            else if (g == 2) warp_apply<2>(S, ldS, j, rows, cols, tj, G, w);
-            else if (g == 3) warp_apply<3>(S, ldS, j, rows, cols, tj, G, w);
+            if (g == 1) warp_apply<1>(S, ldS, j, rows, cols, rf, G, w, &synced, &qj);
+            else if (g == 2) warp_apply<2>(S, ldS, j, rows, cols, rf, G, w, &synced, &qj);
+            else if (g == 3) warp_apply<3>(S, ldS, j, rows, cols, rf, G, w, &synced, &qj);
+            if (!synced) q_sync();                     // exactly one sync per step
         }
         __syncthreads();
     }
+}
+
+// After householder_block: tau[c] = -d^2 q, sc[c] = 1/d (= beta q, 1 for a
+// zero column) and the Gram entries G(c, j) = v_c^T v_j = sc_c sc_j
+// vh_c^T vh_j (strict upper, ld w).  The caller scales x by sc when it writes
+// V out.  Ends with a CTA barrier.
+template <class Real>
+__device__ void finish_block(const Real *S, int ldS, int w, const Refl<Real> &rf, Real *G) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int c = tid; c < w; c += nthr) {
+        const Real q = rf.q[c], d = rf.d[c], bd = rf.bd[c];
+        rf.tau[c] = -(d * d) * q;
+        rf.sc[c] = bd == Real(0) ? Real(1) : S[c + (size_t)c * ldS] * q;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < w * w; idx += nthr) {
+        const int c = idx % w, j = idx / w;
+        if (c < j) G[idx] *= rf.sc[c] * rf.sc[j];
+    }
+    __syncthreads();
 }
 
 // The kernel T of Q = I - V T V^T from tau and the strict upper Gram matrix
@@ -378,7 +434,8 @@ __device__ void build_t(Real *T, const Real *G, const Real *tau, Real *M, int w)
     }
 }
 
-// Up kernel shared memory: S (ldS x w), then T, G (w x w each), tau (w).
+// Up kernel shared memory: S (ldS x w), then T, G (w x w each), then the
+// per-column reflector data (Refl: tau, d, beta*d, q, 1/d; w each).
 template <class Real>
 __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -387,7 +444,8 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
     Real *S = smem;
     Real *T = S + (size_t)ldS * w;
     Real *G = T + w * w;
-    Real *tau = G + w * w;
+    Real *aux = G + w * w;
+    const Refl<Real> rf{aux, aux + w, aux + 2 * w, aux + 3 * w, aux + 4 * w};
     __shared__ int s_last;
 
     const int leaf = blockIdx.x;
@@ -397,18 +455,25 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
 
     load_block(S, ldS, p.A + r0, p.lda, h, w);
     __syncthreads();
-    householder_block(S, ldS, w, LeafRows{h}, tau, G);
+    householder_block(S, ldS, w, LeafRows{h}, rf, G);
+    finish_block(S, ldS, w, rf, G);
 
-    // V_p (strict lower) and R_p (upper) back to the panel rows, R_p to the tree;
-    // then T_p, with the leaf block's shared memory as scratch.  Leaf 0 also
-    // keeps a copy of its top w x w block of V: every CTA of the downsweep
-    // reads it to form X while CTA 0 overwrites those rows of the panel.
-    for (int c = 0; c < w; ++c)
-        for (int r = tid; r < h; r += nthr) p.A[(r0 + r) + c * p.lda] = S[(size_t)c * ldS + r];
+    // V_p (strict lower, normalised here) and R_p (upper) back to the panel
+    // rows, R_p to the tree; then T_p, with the leaf block's shared memory as
+    // scratch.  Leaf 0 also keeps a copy of its top w x w block of V: every
+    // CTA of the downsweep reads it to form X while CTA 0 overwrites those
+    // rows of the panel.
+    for (int c = 0; c < w; ++c) {
+        const Real sc = rf.sc[c];
+        for (int r = tid; r < h; r += nthr) {
+            const Real x = S[(size_t)c * ldS + r];
+            p.A[(r0 + r) + c * p.lda] = (r > c) ? x * sc : x;
+        }
+    }
     if (leaf == 0)
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int i = idx % w, c = idx / w;
-            p.wsX[idx] = (i > c) ? S[(size_t)c * ldS + i] : Real(0);
+            p.wsX[idx] = (i > c) ? S[(size_t)c * ldS + i] * rf.sc[c] : Real(0);
         }
     {
         Real *Rn = p.wsR + (size_t)leaf * ww;
@@ -418,7 +483,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
         }
     }
     __syncthreads();
-    build_t(T, G, tau, S, w);
+    build_t(T, G, rf.tau, S, w);
     {
         Real *Tn = p.wsT + (size_t)leaf * ww;
         for (int idx = tid; idx < w * w; idx += nthr) Tn[idx] = T[idx];
@@ -445,7 +510,8 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
             if (tid == 0) p.counters[pidx - p.P] = 0u;
             load_stack(S, ldS, p.wsR + (size_t)(off + first) * ww, cnt, w);   // the children's R, stacked
             __syncthreads();
-            householder_block(S, ldS, w, MergeRows{w, cnt}, tau, G);
+            householder_block(S, ldS, w, MergeRows{w, cnt}, rf, G);
+            finish_block(S, ldS, w, rf, G);
             Real *Rn = p.wsR + (size_t)pidx * ww, *Tn = p.wsT + (size_t)pidx * ww;
             Real *Yn = p.wsY + (size_t)(pidx - p.P) * (p.k - 1) * ww;
             for (int idx = tid; idx < w * w; idx += nthr) {
@@ -455,10 +521,10 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
             for (int b = 1; b < cnt; ++b)
                 for (int idx = tid; idx < w * w; idx += nthr) {
                     const int i = idx % w, c = idx / w;
-                    Yn[(size_t)(b - 1) * ww + idx] = (i <= c) ? S[(size_t)c * ldS + b * w + i] : Real(0);
+                    Yn[(size_t)(b - 1) * ww + idx] = (i <= c) ? S[(size_t)c * ldS + b * w + i] * rf.sc[c] : Real(0);
                 }
             __syncthreads();
-            build_t(T, G, tau, S, w);
+            build_t(T, G, rf.tau, S, w);
             for (int idx = tid; idx < w * w; idx += nthr) Tn[idx] = T[idx];
         } else {
             // single child: the node is the identity, its R passes through
@@ -733,7 +799,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
     }
 }
 
-size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + w); }
+size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + 5 * (size_t)w); }
 size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 5 * (size_t)w * w + 2 * w); }
 
 constexpr size_t kSmemCap = 200 * 1024;
@@ -752,7 +818,7 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     pl.k = k;
     // tallest leaf that every kernel's shared memory can hold
     const size_t cap_el = kSmemCap / sizeof(double);
-    int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + w)) / w);                      // up
+    int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + 5 * (size_t)w)) / w);          // up
     hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 5 * (size_t)w * w - 2 * w) / w));   // down + recon
     if (hcap < w) return false;
     // default: about one leaf per SM (the leaf phase is the only one that
