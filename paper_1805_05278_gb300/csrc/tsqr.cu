@@ -273,17 +273,20 @@ template <class Real, class Rows>
 __device__ void pivot_step(Real *S, int ldS, int j, int w, const Rows &rows, const Refl<Real> &rf) {
     const int lane = threadIdx.x & 31, c = j + 1;
     const Real dj = rf.d[j];
+    const Real *vj = S + (size_t)j * ldS;
+    Real *col = S + (size_t)c * ldS;
+    Real acc = Real(0);
+    if (c < w) rows.each_with_pivot(j, lane, [&](int r, bool piv) { acc = rfma(piv ? dj : vj[r], col[r], acc); });
+    // the reciprocal and the reduction are independent chains: nothing
+    // between them, so their latencies overlap
     const Real qj = q_of(rf.bd[j]);
+    acc = warp_sum(acc);
     if (lane == 0) rf.q[j] = qj;
     __syncwarp();
     __threadfence_block();
     q_arrive();
     if (c >= w) return;
-    const Real *vj = S + (size_t)j * ldS;
-    Real *col = S + (size_t)c * ldS;
-    Real acc = Real(0);
-    rows.each_with_pivot(j, lane, [&](int r, bool piv) { acc = rfma(piv ? dj : vj[r], col[r], acc); });
-    const Real f = qj * warp_sum(acc);
+    const Real f = qj * acc;
     Real part = Real(0);
     rows.each_with_pivot(j, lane, [&](int r, bool piv) {
         const Real x = rfma(f, piv ? dj : vj[r], col[r]);
@@ -415,7 +418,7 @@ __device__ void build_t(Real *T, const Real *G, const Real *tau, Real *M, int w)
         const int s2 = 2 * s;
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int row = idx % w, col = idx / w;
-            const int b1 = (row / s2) * s2 + s;
+            const int b1 = (row & ~(s2 - 1)) + s;
             if (row >= b1 || col < b1 || col >= b1 + s) continue;
             Real acc = Real(0);   // (G12 T22)(row, col)
             for (int l = b1; l <= col; ++l) acc = rfma(G[row + l * w], T[l + col * w], acc);
@@ -424,7 +427,7 @@ __device__ void build_t(Real *T, const Real *G, const Real *tau, Real *M, int w)
         __syncthreads();
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int row = idx % w, col = idx / w;
-            const int b1 = (row / s2) * s2 + s;
+            const int b1 = (row & ~(s2 - 1)) + s;
             if (row >= b1 || col < b1 || col >= b1 + s) continue;
             Real acc = Real(0);   // (T11 M)(row, col)
             for (int l = row; l < b1; ++l) acc = rfma(T[row + l * w], M[l + col * w], acc);
@@ -565,7 +568,7 @@ __device__ void unit_lower_inverse(const Real *L, Real *Li, Real *M, int w) {
         const int s2 = 2 * s;
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int row = idx % w, col = idx / w;
-            const int b1 = (col / s2) * s2 + s;   // pair (b0 = b1 - s, b1), col in block 0, row in block 1
+            const int b1 = (col & ~(s2 - 1)) + s;   // pair (b0 = b1 - s, b1), col in block 0, row in block 1
             if (col >= b1 || row < b1 || row >= b1 + s) continue;
             Real acc = Real(0);   // (L21 Li11)(row, col)
             for (int l = col; l < b1; ++l) acc = rfma(L[row + l * w], Li[l + col * w], acc);
@@ -574,7 +577,7 @@ __device__ void unit_lower_inverse(const Real *L, Real *Li, Real *M, int w) {
         __syncthreads();
         for (int idx = tid; idx < w * w; idx += nthr) {
             const int row = idx % w, col = idx / w;
-            const int b1 = (col / s2) * s2 + s;
+            const int b1 = (col & ~(s2 - 1)) + s;
             if (col >= b1 || row < b1 || row >= b1 + s) continue;
             Real acc = M[idx];   // Li22(row,row) = 1
             for (int l = b1; l < row; ++l) acc = rfma(Li[row + l * w], M[l + col * w], acc);
@@ -723,25 +726,35 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
         X[idx] = B[idx] - s;
     }
     __syncthreads();
-    // X + S = L U
+    // X + S = L U.  Per step one thread adds the sign to the pivot and takes
+    // its reciprocal; then every entry of the trailing block forms its own
+    // multiplier l_i = X(i, j) / pivot and is updated in the same pass, the
+    // multipliers going to C, so X's column j and row j are only read during
+    // the step (two barriers per step).  C is free here.
     for (int j = 0; j < w; ++j) {
         if (tid == 0) {
             const Real sg = X[j + j * w] < Real(0) ? -Real(1) : Real(1);
             Sg[j] = sg;
-            X[j + j * w] += sg;
+            const Real piv = X[j + j * w] + sg;
+            X[j + j * w] = piv;
+            rU[j] = real_rcp(piv);
         }
         __syncthreads();
-        const Real piv = X[j + j * w];
-        for (int i = j + 1 + tid; i < w; i += nthr) X[i + j * w] /= piv;
-        __syncthreads();
+        const Real rp = rU[j];
         const int rem = w - j - 1;
-        for (int idx = tid; idx < rem * rem; idx += nthr) {
-            const int i = j + 1 + idx % rem, c = j + 1 + idx / rem;
-            X[i + c * w] = rfma(-X[i + j * w], X[j + c * w], X[i + c * w]);
+        for (int idx = tid; idx < rem * (rem + 1); idx += nthr) {
+            const int i = j + 1 + idx % rem, c = j + idx / rem;
+            const Real l = X[i + j * w] * rp;
+            if (c == j) C[i + j * w] = l;
+            else X[i + c * w] = rfma(-l, X[j + c * w], X[i + c * w]);
         }
         __syncthreads();
     }
-    for (int j = tid; j < w; j += nthr) rU[j] = real_rcp(X[j + j * w]);
+    for (int idx = tid; idx < w * w; idx += nthr) {
+        const int i = idx % w, c = idx / w;
+        if (i > c) X[idx] = C[idx];                           // L below the diagonal
+    }
+    __syncthreads();
     if (leaf == 0) {
         // T = U S L^{-T}: T(i, c) = sum_{l=i}^{c} U(i, l) S_l Li(c, l)
         unit_lower_inverse(X, Li, C, w);
