@@ -14,12 +14,15 @@
 //                      forms the top w x w block X of W = Q [I; 0] (from the
 //                      copy of leaf 0's top V block the upsweep kept), factors
 //                      X + S = LU with S_jj = sgn(X^_jj) added before
-//                      eliminating column j, walks to its own leaf applying
-//                      the node Q-factors to B^(L) = I, forms its rows W_p
-//                      and writes V_p = W_p U^{-1}; CTA 0 writes T = U S L^{-T},
-//                      V_top = L and R = -S R^(L).  The small LU and the walk
-//                      to leaf 0 are repeated by every CTA instead of being
-//                      broadcast, so the launch needs no inter-CTA waiting.
+//                      eliminating column j, and inverts U.  It then walks to
+//                      its own leaf applying the node Q-factors to
+//                      B^(L) = U^{-1} instead of I - the shortcut noted at the
+//                      end of Appendix C - so its rows of Q [U^{-1}; 0] are
+//                      V_p = W_p U^{-1} directly, with no per-row triangular
+//                      solve.  CTA 0 writes T = U S L^{-T}, V_top = L and
+//                      R = -S R^(L).  The small LU and the walk to leaf 0 are
+//                      repeated by every CTA instead of being broadcast, so
+//                      the launch needs no inter-CTA waiting.
 //
 // Merged nodes exploit the structure of stacked triangles: the Householder
 // vector of column j has a 1 in row j of the first triangle and non-zeros
@@ -588,12 +591,14 @@ __device__ void unit_lower_inverse(const Real *L, Real *Li, Real *M, int w) {
 }
 
 // B <- (the node Q-factors along the root-to-`target` path) applied to
-// B = I at the root (Appendix C.2, downsweep): each node on the path gives its
-// child [B_0; B_1; ...] = (I - V T V^T)[B; 0] = [B - T B; -Y_1 T B; ...].  T, Y
-// and I are upper triangular, so B stays upper triangular and each product
-// costs about w^3/6 multiply-adds.  C, M: w x w scratch.
+// B = I at the root, or to the upper triangular Binit (Appendix C.2,
+// downsweep): each node on the path gives its child [B_0; B_1; ...] =
+// (I - V T V^T)[B; 0] = [B - T B; -Y_1 T B; ...].  T, Y and B are upper
+// triangular, so B stays upper triangular and each product costs about
+// w^3/6 multiply-adds.  C, M: w x w scratch.
 template <class Real>
-__device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real *C, Real *M, Real *Yb) {
+__device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real *C, Real *M, Real *Yb,
+                          const Real *Binit = nullptr) {
     const int w = p.w, tid = threadIdx.x, nthr = blockDim.x;
     const int ww = w * w;
     constexpr int kPer = (kMaxPanel * kMaxPanel + kThreads - 1) / kThreads;   // entries per thread
@@ -628,7 +633,7 @@ __device__ void walk_path(const TsqrParamsT<Real> &p, int target, Real *B, Real 
             }
         }
     };
-    for (int idx = tid; idx < ww; idx += nthr) B[idx] = (idx % w == idx / w) ? Real(1) : Real(0);
+    for (int idx = tid; idx < ww; idx += nthr) B[idx] = Binit ? Binit[idx] : ((idx % w == idx / w) ? Real(1) : Real(0));
     int cur = next_merge(p.L - 1);
     if (cur >= 0) fetch(cur);
     __syncthreads();
@@ -703,7 +708,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
     const size_t ww = (size_t)w * w;
     Real *B = smem;          // w x w: B of the path walked
     Real *C = B + ww;        // w x w scratch
-    Real *M = C + ww;        // w x w: T, then Z
+    Real *M = C + ww;        // w x w: T, then Z, then U^{-1}, then T_p and Z_p
     Real *X = M + ww;        // w x w: X, then L (strict lower) and U
     Real *Li = X + ww;       // w x w: leaf 0's top V block, then L^{-1}
     Real *Sg = Li + ww;      // w signs
@@ -755,6 +760,11 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
         if (i > c) X[idx] = C[idx];                           // L below the diagonal
     }
     __syncthreads();
+    // U^{-1} into M (Z of leaf 0 is no longer needed): the inverse of the
+    // upper triangular matrix with strict upper part U and diagonal 1/rU,
+    // which is what build_t computes from (G, tau)
+    Real *Ui = M;
+    build_t(Ui, X, rU, C, w);
     if (leaf == 0) {
         // T = U S L^{-T}: T(i, c) = sum_{l=i}^{c} U(i, l) S_l Li(c, l)
         unit_lower_inverse(X, Li, C, w);
@@ -764,12 +774,18 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
             for (int l = i; l <= c; ++l) t = rfma(X[i + l * w] * Sg[l], (l == c) ? Real(1) : Li[c + l * w], t);
             p.Tout[i + c * p.ldt] = t;
         }
+        __syncthreads();
+        upper_upper(B, Ui, C, w, Real(1));                    // leaf 0: B_0 U^{-1}
+        __syncthreads();
+        for (int idx = tid; idx < w * w; idx += nthr) B[idx] = C[idx];
     } else {
-        walk_path(p, leaf, B, C, M, Li);                     // leaf 0 keeps B_0; Li is free here
+        // from B^(L) = U^{-1}: the walk copies Ui into B before it first
+        // stages a node's T in M; Li is free here
+        walk_path(p, leaf, B, C, M, Li, Ui);
     }
     __syncthreads();
 
-    // this leaf: W_p = (I - V_p T_p V_p^T)[B_p; 0], then V rows = W rows U^{-1}
+    // this leaf: V_p = (I - V_p T_p V_p^T)[B_p; 0] with B_p from B^(L) = U^{-1}
     const int64_t r0 = leaf_begin(p.mp, p.P, leaf), r1 = leaf_begin(p.mp, p.P, leaf + 1);
     const int h = (int)(r1 - r0);
     load_block(Vs, ldS, p.A + r0, p.lda, h, w);
@@ -781,18 +797,12 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
     leaf_z(Vs, ldS, B, C, M, w);
     for (int r = tid; r < h; r += nthr) {
         if (r0 + r < w) continue;                           // leaf 0's top block: L \ R below
-        // W(r, c) = [B; 0](r, c) - sum_{i <= min(r, c)} Vhat(r, i) Z(i, c), in place, c descending
+        // V(r, c) = [B; 0](r, c) - sum_{i <= min(r, c)} Vhat(r, i) Z(i, c), in place, c descending
         for (int c = w - 1; c >= 0; --c) {
             Real s = (r <= c) ? M[r + c * w] : Real(0);
             const int iend = min(r, c + 1);
             for (int i = 0; i < iend; ++i) s = rfma(Vs[(size_t)i * ldS + r], M[i + c * w], s);
             Vs[(size_t)c * ldS + r] = ((r < w) ? B[r + c * w] : Real(0)) - s;
-        }
-        // V(r, :) U = W(r, :), in place, j ascending
-        for (int j = 0; j < w; ++j) {
-            Real v = Vs[(size_t)j * ldS + r];
-            for (int l = 0; l < j; ++l) v = rfma(-Vs[(size_t)l * ldS + r], X[l + j * w], v);
-            Vs[(size_t)j * ldS + r] = v * rU[j];
         }
     }
     __syncthreads();
@@ -926,10 +936,10 @@ gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &pl, Real *A, int64_t lda,
 
     trace_begin(ex, FAM_TSQR_DOWN);
     tsqr_down_kernel<Real><<<pl.P, kThreads, pl.smem_down, ex.stream>>>(p);
-    // per leaf: two path walks (~2 L products of w^3/6 each), X and its LU
-    // (w^3/3), the leaf's W (~m_p w^2) and V = W U^{-1} (~m_p w^2 / 2)
+    // per leaf: two path walks (~2 L products of w^3/6 each), X, its LU and
+    // U^{-1} (~2 w^3/3), and the leaf's rows of Q [U^{-1}; 0] (~m_p w^2)
     st = trace_end(ex, FAM_TSQR_DOWN,
-                   3.0 * mp * ww + (double)pl.P * ((4.0 * pl.L + 2.0) * ww * w / 3.0 + 2.0 * ww * w / 3.0),
+                   2.0 * mp * ww + (double)pl.P * ((4.0 * pl.L + 4.0) * ww * w / 3.0),
                    (double)sizeof(Real) * (2.0 * mp * w + 2.0 * (double)pl.nodes * ww));
     return st;
 }
