@@ -182,7 +182,11 @@ GBQR_API gbqr_status gbqr_sync(gbqr_ctx *ctx, gbqr_info *info);
  * R = -S R_tree, V = W U^{-1} (Appendix C).
  * A and T may instead both be HOST pointers (pageable or pinned): the call
  * then stages them through device workspace, copies the results back and
- * returns after the stream has synchronised.
+ * returns after the stream has synchronised.  With page-locked buffers and
+ * the PANEL layout with look-ahead, the copies overlap the factorization:
+ * panels 0 and 1 arrive first and the rest behind them on a copy stream,
+ * and each panel's columns and T block are copied back as soon as that
+ * panel is factored.
  * Wide A (m < n, Section 2.1): the leading m x m block is factored as above
  * and the m reflectors are applied to the remaining n - m columns, giving
  * R = [R1, Q^T A2] (upper trapezoidal) over A; T then holds the min(m, n) = m

@@ -199,6 +199,8 @@ struct gbqr_ctx {
     bool tracing = false;
     cudaStream_t side = nullptr;          // high-priority stream for look-ahead panels
     cudaEvent_t ev_panel = nullptr, ev_ready = nullptr, ev_fork = nullptr;
+    cudaStream_t copy = nullptr;          // host <-> device copies of the staged path
+    cudaEvent_t ev_in0 = nullptr, ev_in1 = nullptr, ev_in = nullptr;   // staged input: panel 0, panel 1, the rest
     std::vector<cudaStream_t> lanes;      // batched factorization: one stream per lane
     std::vector<cudaEvent_t> lane_done;
     mutable std::mutex tuned_mu;           // autotuner results (gbqr_autotune*)
@@ -337,6 +339,7 @@ gbqr_status ensure_workspace(gbqr_ctx *cx, size_t bytes) {
     if (cx->ws) {
         cudaStreamSynchronize(cx->stream);
         if (cx->side) cudaStreamSynchronize(cx->side);
+        if (cx->copy) cudaStreamSynchronize(cx->copy);
         for (auto st : cx->lanes) cudaStreamSynchronize(st);
         cudaFree(cx->ws);
         cx->ws = nullptr;
@@ -534,10 +537,49 @@ gbqr_status zero_below_blocks(Work &w, int64_t rows, int64_t n, int64_t nb, Real
     return trace_end(w.ex, FAM_OTHER, 0.0, (double)sizeof(Real) / 2.0 * (double)total);
 }
 
+// Host buffers of a staged factorization (PANEL layout with look-ahead):
+// their panels travel on the context's copy stream, overlapped with the
+// factorization of the others.
+struct HostIO {
+    double *A; int64_t lda;   // m x n
+    double *T; int64_t ldt;   // trows x n
+};
+
+// Column blocks [c0, c0 + nc) of the m-row host matrix to the device, each
+// scanned for non-finite entries on arrival; `done` marks the last one.
+gbqr_status stage_in(Work &w, const HostIO &io, double *A, int64_t lda, int64_t m, int64_t c0, int64_t nc,
+                     cudaEvent_t done) {
+    gbqr_ctx *cx = w.cx;
+    if (nc > 0) {
+        if (cudaMemcpy2DAsync(A + c0 * lda, lda * 8, io.A + c0 * io.lda, io.lda * 8, m * 8, nc,
+                              cudaMemcpyHostToDevice, cx->copy) != cudaSuccess)
+            return GBQR_ECUDA;
+        Exec ce = w.ex;
+        ce.stream = cx->copy;
+        TRY(scan_nonfinite(ce, m, nc, A + c0 * lda, lda, &cx->dinfo->nonfinite));
+    }
+    return cudaEventRecord(done, cx->copy) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+}
+
+// Panel [j0, j0 + wd) is final once its factorization (ev_panel, just
+// recorded) is done: its columns and T block go back while later panels run.
+gbqr_status stage_out(Work &w, const HostIO &io, const double *A, int64_t lda, const double *T, int64_t ldt,
+                      int64_t m, int64_t trows, int64_t j0, int64_t wd) {
+    gbqr_ctx *cx = w.cx;
+    if (cudaStreamWaitEvent(cx->copy, cx->ev_panel, 0) != cudaSuccess ||
+        cudaMemcpy2DAsync(io.A + j0 * io.lda, io.lda * 8, A + j0 * lda, lda * 8, m * 8, wd, cudaMemcpyDeviceToHost,
+                          cx->copy) != cudaSuccess ||
+        cudaMemcpy2DAsync(io.T + j0 * io.ldt, io.ldt * 8, T + j0 * ldt, ldt * 8, trows * 8, wd,
+                          cudaMemcpyDeviceToHost, cx->copy) != cudaSuccess)
+        return GBQR_ECUDA;
+    return GBQR_OK;
+}
+
 template <class Real>
-gbqr_status factor_device(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, Real *T, int64_t ldt, int layout) {
+gbqr_status factor_device(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, Real *T, int64_t ldt, int layout,
+                          const HostIO *io = nullptr) {
     DeviceInfo *di = w.cx->dinfo;
-    TRY(scan_nonfinite(w.ex, m, n, A, lda, &di->nonfinite));
+    if (!io) TRY(scan_nonfinite(w.ex, m, n, A, lda, &di->nonfinite));
     if (layout == GBQR_T_FULL) {
         TRY(zero_below_blocks(w, n, n, std::max<int64_t>(n, 1), T, ldt));
         return qr_eg(w, m, n, A, lda, T, ldt);
@@ -563,10 +605,31 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, R
     // stream.  Event fork/join only, so the sequence is graph-capturable.
     Work wp = w.lane2();
     const cudaStream_t ms = w.ex.stream, ss = cx->side;
+    if (io) {
+        // staged: the copy stream starts after the work already on the main
+        // stream (the staging buffer may still be in use), then brings in
+        // panel 0, panel 1 and the rest, in that order
+        if constexpr (!std::is_same<Real, double>::value) return GBQR_EINVAL;
+        else {
+            const int64_t b0 = nb, b1 = std::min<int64_t>(nb, n - b0);
+            if (cudaEventRecord(cx->ev_in0, ms) != cudaSuccess || cudaStreamWaitEvent(cx->copy, cx->ev_in0, 0) != cudaSuccess)
+                return GBQR_ECUDA;
+            TRY(stage_in(w, *io, A, lda, m, 0, b0, cx->ev_in0));
+            TRY(stage_in(w, *io, A, lda, m, b0, b1, cx->ev_in1));
+            TRY(stage_in(w, *io, A, lda, m, b0 + b1, n - b0 - b1, cx->ev_in));
+            if (cudaStreamWaitEvent(ms, cx->ev_in0, 0) != cudaSuccess) return GBQR_ECUDA;
+        }
+    }
+    auto panel_out = [&](int64_t j0, int64_t wd) -> gbqr_status {
+        if constexpr (std::is_same<Real, double>::value)
+            if (io) return stage_out(w, *io, A, lda, T, ldt, m, ldt, j0, wd);
+        return GBQR_OK;
+    };
     if (cudaEventRecord(cx->ev_fork, ms) != cudaSuccess || cudaStreamWaitEvent(ss, cx->ev_fork, 0) != cudaSuccess)
         return GBQR_ECUDA;
     TRY(qr_eg(wp, m, std::min<int64_t>(nb, n), A, lda, T, ldt));
     if (cudaEventRecord(cx->ev_panel, ss) != cudaSuccess) return GBQR_ECUDA;
+    TRY(panel_out(0, std::min<int64_t>(nb, n)));
     for (int64_t k = 0; k < npan; ++k) {
         const int64_t j0 = k * nb, wd = std::min<int64_t>(nb, n - j0);
         if (cudaStreamWaitEvent(ms, cx->ev_panel, 0) != cudaSuccess) return GBQR_ECUDA;   // panel k done
@@ -574,6 +637,7 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, R
         const int64_t j1 = j0 + wd, w1 = std::min<int64_t>(nb, n - j1);
         const Real *Vk = A + j0 + j0 * lda;
         const Real *Tk = T + j0 * ldt;
+        if (io && k == 0 && cudaStreamWaitEvent(ms, cx->ev_in1, 0) != cudaSuccess) return GBQR_ECUDA;
         // panel k+1's columns first ...
         TRY(apply_block(w, true, m - j0, w1, wd, Vk, lda, Tk, ldt, A + j0 + j1 * lda, lda, w.pr.nsplit));
         if (cudaEventRecord(cx->ev_ready, ms) != cudaSuccess || cudaStreamWaitEvent(ss, cx->ev_ready, 0) != cudaSuccess)
@@ -581,6 +645,8 @@ gbqr_status factor_device(Work &w, int64_t m, int64_t n, Real *A, int64_t lda, R
         // ... then panel k+1 on the side stream, concurrently with the rest of the update
         TRY(qr_eg(wp, m - j1, w1, A + j1 + j1 * lda, lda, T + j1 * ldt, ldt));
         if (cudaEventRecord(cx->ev_panel, ss) != cudaSuccess) return GBQR_ECUDA;
+        TRY(panel_out(j1, w1));
+        if (io && k == 0 && cudaStreamWaitEvent(ms, cx->ev_in, 0) != cudaSuccess) return GBQR_ECUDA;
         if (j1 + w1 < n)
             TRY(apply_block(w, true, m - j0, n - j1 - w1, wd, Vk, lda, Tk, ldt, A + j0 + (j1 + w1) * lda, lda,
                             w.pr.nsplit));
@@ -615,6 +681,14 @@ bool is_host_pointer(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return true; }
     return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+}
+
+// Page-locked host memory: asynchronous copies from and to it do not block
+// the calling thread.
+bool is_pinned_host(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeHost;
 }
 
 gbqr_status check_layout_args(int64_t m, int64_t n, int64_t lda, int64_t ldt, int layout, int64_t nb) {
@@ -683,7 +757,11 @@ gbqr_status gbqr_create(gbqr_ctx **out, int device, void *cuda_stream) {
         cudaStreamCreateWithPriority(&cx->side, cudaStreamNonBlocking, greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&cx->ev_panel, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&cx->ev_ready, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&cx->ev_fork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&cx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&cx->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cx->ev_in0, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cx->ev_in1, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&cx->ev_in, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         gbqr_destroy(cx);
         return GBQR_ECUDA;
@@ -698,6 +776,7 @@ gbqr_status gbqr_destroy(gbqr_ctx *cx) {
     cudaSetDevice(cx->device);
     cudaStreamSynchronize(cx->stream);
     if (cx->side) cudaStreamSynchronize(cx->side);
+    if (cx->copy) cudaStreamSynchronize(cx->copy);
     if (cx->ws_owned && cx->ws) cudaFree(cx->ws);
     cx->ws = nullptr;
     if (cx->dinfo) cudaFree(cx->dinfo);
@@ -705,6 +784,10 @@ gbqr_status gbqr_destroy(gbqr_ctx *cx) {
     if (cx->ev_ready) cudaEventDestroy(cx->ev_ready);
     if (cx->ev_fork) cudaEventDestroy(cx->ev_fork);
     if (cx->side) cudaStreamDestroy(cx->side);
+    if (cx->ev_in0) cudaEventDestroy(cx->ev_in0);
+    if (cx->ev_in1) cudaEventDestroy(cx->ev_in1);
+    if (cx->ev_in) cudaEventDestroy(cx->ev_in);
+    if (cx->copy) cudaStreamDestroy(cx->copy);
     for (auto st : cx->lanes) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
     for (auto ev : cx->lane_done) cudaEventDestroy(ev);
     delete cx->tracer;
@@ -724,6 +807,7 @@ gbqr_status gbqr_set_workspace(gbqr_ctx *cx, void *ptr, size_t bytes) {
     if (cx->ws_owned && cx->ws) {
         cudaStreamSynchronize(cx->stream);
         if (cx->side) cudaStreamSynchronize(cx->side);
+        if (cx->copy) cudaStreamSynchronize(cx->copy);
         cudaFree(cx->ws);
     }
     cx->ws = (char *)ptr;
@@ -808,6 +892,16 @@ gbqr_status gbqr::factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, 
     // host buffers: stage through the workspace, factor, copy back, synchronise
     const int64_t trows = (t_layout == GBQR_T_FULL) ? n : std::min<int64_t>(pr.nb, n);
     if ((size_t)trows * (size_t)n > w.L.n_bigT) return GBQR_ENOMEM;
+    if (t_layout == GBQR_T_PANEL && pr.lookahead && cx->side && cx->copy && n > trows && is_pinned_host(A) &&
+        is_pinned_host(T)) {
+        // PANEL with look-ahead and page-locked buffers: panels in and out on
+        // the copy stream, overlapped with the factorization (factor_device)
+        const HostIO io{A, lda, T, ldt};
+        TRY(factor_device(w, m, n, w.bigA, m, w.bigT, trows, t_layout, &io));
+        if (cudaStreamSynchronize(cx->copy) != cudaSuccess || cudaStreamSynchronize(cx->side) != cudaSuccess)
+            return GBQR_ECUDA;
+        return cudaStreamSynchronize(cx->stream) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+    }
     if (cudaMemcpy2DAsync(w.bigA, m * 8, A, lda * 8, m * 8, n, cudaMemcpyHostToDevice, cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
     TRY(factor_device(w, m, n, w.bigA, m, w.bigT, trows, t_layout));

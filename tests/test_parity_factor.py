@@ -179,6 +179,34 @@ def test_host_pointers(gb, ctx, orc):
     _gpu.compare_factor(a, vr, t, gb.GBQR_T_FULL, 50, orc, "host pointers")
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+@pytest.mark.parametrize("m,n,nb,pad", [(1500, 300, 64, 0), (900, 250, 32, 7), (700, 130, 64, 3), (2304, 320, 128, 5)])
+def test_host_pointers_panel(gb, ctx, orc, m, n, nb, pad, pinned):
+    """Host A and T in the PANEL layout with look-ahead.  Page-locked buffers
+    take the overlapped path (panels in and out on the copy stream while
+    others are factored), pageable ones the plain staged path; both must
+    give the oracle's factorization, with ragged last panels and padded
+    leading dimensions whose padding stays untouched."""
+    import ctypes
+    import torch
+    a = workloads.gaussian(m, n, 23)
+    lda, trows = m + pad, min(nb, n)
+    ldt = trows + pad
+    Ah = torch.full((n, lda), float("nan"), dtype=torch.float64)
+    Th = torch.full((n, ldt), float("nan"), dtype=torch.float64)
+    if pinned:
+        Ah, Th = Ah.pin_memory(), Th.pin_memory()
+    Ah[:, :m] = torch.from_numpy(np.ascontiguousarray(a.T))
+    o = gb.opts(panel_nb=nb)
+    st = gb.gbqr_factor(ctx.handle, m, n, ctypes.c_void_p(Ah.data_ptr()), lda, ctypes.c_void_p(Th.data_ptr()), ldt,
+                        gb.GBQR_T_PANEL, ctypes.byref(o))
+    assert st == gb.GBQR_OK
+    assert torch.isnan(Ah[:, m:]).all() and torch.isnan(Th[:, trows:]).all(), "padding was written"
+    vr = Ah[:, :m].numpy().T.copy(order="F")
+    t = Th[:, :trows].numpy().T.copy(order="F")
+    _gpu.compare_factor(a, vr, t, gb.GBQR_T_PANEL, nb, orc, f"host panel pinned={pinned}")
+
+
 @pytest.mark.parametrize("lookahead", [0, -1])
 @pytest.mark.parametrize("m,n,nb", [(2000, 300, 16), (640, 640, 64), (5000, 129, 32)])
 def test_lookahead_on_and_off(gb, ctx, orc, m, n, nb, lookahead):
