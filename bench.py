@@ -594,7 +594,7 @@ def run_gbqr(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed,
                        "t_layout": args.layout, "panel_nb": nb if layout == gb.GBQR_T_PANEL else None,
-                       "cutoff_b": o.cutoff_b or 16, "fanout": o.fanout or 8, "leaf_rows": o.leaf_rows,
+                       "cutoff_b": o.cutoff_b or 16, "fanout": o.fanout or "adaptive", "leaf_rows": o.leaf_rows,
                        "lookahead": o.lookahead, "fp64_gemm": "dmma" if o.fp64_gemm == gb.GBQR_GEMM_DMMA else "dfma",
                        "autotuned": tuned is not None, "autotune_ms": tune_ms, "parallelism": f"replicas x{world}",
                        "l2": "inputs (%.0f MB) larger than L2, no flush" % (w.m * w.n * 8 / 1e6),

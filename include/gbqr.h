@@ -95,8 +95,9 @@ typedef struct {
                            (Algorithm 2); 1 <= b <= 64 */
     int32_t panel_nb;   /* GBQR_T_PANEL: top-level panel width nb (>= 1) */
     int32_t leaf_rows;  /* TSQR leaf height target m_p (>= b; Section 5 needs m_p >= n) */
-    int32_t fanout;     /* TSQR reduction-tree fan-out k (2..8; the paper's
-                           binomial tree is k = 2, Appendix C.1) */
+    int32_t fanout;     /* TSQR reduction-tree fan-out k (2..16; the paper's
+                           binomial tree is k = 2, Appendix C.1; 0 = the
+                           fewest merge levels with k <= 16, k >= 8) */
     int32_t lookahead;  /* GBQR_T_PANEL: 0 or 1 = factor panel k+1 on a
                            high-priority internal stream while the rest of
                            panel k's trailing update runs (default); -1 = off */
@@ -332,7 +333,7 @@ GBQR_API gbqr_status gbqr_gemm_split_bf16(gbqr_ctx *ctx, int transa, int64_t M, 
  * tree of Section 5 / Appendix C, the panel width of Section 8.4's
  * right-looking top level) from a cost model of a distributed machine.  Here
  * they are measured: coordinate descent from the library defaults over
- * cutoff_b {8,16,32,64}, fanout {2,4,8}, leaf_rows {default,128,...,1024},
+ * cutoff_b {8,16,32,64}, fanout {adaptive,2,4,8,16}, leaf_rows {default,128,...,1024},
  * and for PANEL panel_nb {64,...,256} and lookahead, and for FP64 the GEMM
  * engine; each candidate is gbqr_factor on a synthetic m x n matrix, timed
  * with CUDA events on the context's stream (best of 2-5 runs after a
@@ -357,7 +358,7 @@ GBQR_API gbqr_status gbqr_autotune(gbqr_ctx *ctx, int64_t m, int64_t n, int t_la
 
 /* The same for gbqr_factor_batched on `count` matrices of shapes (m[i], n[i])
  * (synthetic contents, one buffer): batch_streams {16,...,128}, cutoff_b
- * {8,16,32}, fanout {2,4,8}, leaf_rows {default,256,512}.  Each candidate
+ * {8,16,32}, fanout {adaptive,2,4,8,16}, leaf_rows {default,256,512}.  Each candidate
  * is captured into a CUDA graph on a private stream and its graph launches
  * are timed (the way a batch is meant to run; eager enqueueing of thousands
  * of launches is host-bound).  EBUSY while tracing is on.  Cached per

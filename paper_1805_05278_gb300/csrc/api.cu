@@ -91,7 +91,7 @@ bool resolve(const gbqr_opts *o, int64_t m, int64_t n, Params *p) {
     if (o) {
         if (o->cutoff_b < 0 || o->cutoff_b > kMaxPanel) return false;
         if (o->panel_nb < 0 || o->leaf_rows < 0) return false;
-        if (o->fanout != 0 && (o->fanout < 2 || o->fanout > 8)) return false;
+        if (o->fanout != 0 && (o->fanout < 2 || o->fanout > 16)) return false;
         if (o->cutoff_b) r.b = o->cutoff_b;
         if (o->panel_nb) r.nb = o->panel_nb;
         if (o->leaf_rows) r.leaf_rows = o->leaf_rows;

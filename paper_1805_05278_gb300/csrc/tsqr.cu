@@ -827,6 +827,7 @@ size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 5 
 
 constexpr size_t kSmemCap = 200 * 1024;
 constexpr int kDefaultFanout = 8;
+constexpr int kMaxFanout = 16;
 
 }  // namespace
 
@@ -834,11 +835,6 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     if (w < 1 || w > kMaxPanel || mp < w) return false;
     TsqrPlan pl;
     pl.mp = mp; pl.w = w;
-    // fan-out: as requested, but the merge of k stacked triangles (k*w rows)
-    // must fit the up kernel's shared memory
-    int k = std::min(8, std::max(2, fanout > 0 ? fanout : kDefaultFanout));
-    while (k > 2 && up_smem(k * w, w) > kSmemCap) --k;
-    pl.k = k;
     // tallest leaf that every kernel's shared memory can hold
     const size_t cap_el = kSmemCap / sizeof(double);
     int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + 5 * (size_t)w)) / w);          // up
@@ -859,6 +855,21 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     pl.P = (int)P;
     pl.hmax = (int)((mp + P - 1) / P);
     if (pl.hmax > hcap) return false;
+    // fan-out: as requested (2 .. 16), else the fewest serial merge levels a
+    // fan-out of at most 16 gives, with the smallest such k >= 8: a level
+    // costs a fixed chain of w Householder steps, while a merge grows only
+    // with the k - 1 stacked triangles below its pivots.  The merge of k
+    // stacked triangles (k*w rows) must fit the up kernel's shared memory.
+    auto levels = [&](int kk) { int64_t n = P; int l = 0; while (n > 1) { n = (n + kk - 1) / kk; ++l; } return l; };
+    int k = kDefaultFanout;
+    if (fanout > 0) {
+        k = std::min(kMaxFanout, std::max(2, fanout));
+    } else {
+        for (int c = kDefaultFanout + 1; c <= kMaxFanout; ++c)
+            if (levels(c) < levels(k)) k = c;
+    }
+    while (k > 2 && up_smem(k * w, w) > kSmemCap) --k;
+    pl.k = k;
     pl.ldS = std::max(pl.hmax, pl.k * w);   // up kernel (leaf block or k stacked triangles)
     pl.ldW = pl.hmax;                        // down / recon kernels (leaf block only)
     int64_t nodes = P, Nl = P, L = 0, internal = 0;
@@ -892,14 +903,17 @@ TsqrPlan tsqr_plan_bound(int64_t mp, int w, int leaf_rows, int fanout, int num_s
         if (mp < ww || !tsqr_plan(mp, ww, leaf_rows, fanout, num_sms, &pl)) continue;
         int64_t P = pl.P;
         if (leaf_rows <= 0) P = std::max<int64_t>(P, std::min<int64_t>(sms, mp / ww));
-        int64_t nodes = P, Nl = P, internal = 0;
-        while (Nl > 1) { Nl = (Nl + pl.k - 1) / pl.k; nodes += Nl; internal += Nl; }
+        // a shorter panel may get another fan-out: bound over all of them
         const size_t w2 = (size_t)ww * ww;
-        best.nR = std::max(best.nR, (size_t)nodes * w2);
-        best.nT = std::max(best.nT, (size_t)nodes * w2);
-        best.nY = std::max(best.nY, (size_t)std::max<int64_t>(internal, 1) * (pl.k - 1) * w2);
+        for (int k = 2; k <= kMaxFanout; ++k) {
+            int64_t nodes = P, Nl = P, internal = 0;
+            while (Nl > 1) { Nl = (Nl + k - 1) / k; nodes += Nl; internal += Nl; }
+            best.nR = std::max(best.nR, (size_t)nodes * w2);
+            best.nT = std::max(best.nT, (size_t)nodes * w2);
+            best.nY = std::max(best.nY, (size_t)std::max<int64_t>(internal, 1) * (k - 1) * w2);
+            best.ncount = std::max(best.ncount, (size_t)std::max<int64_t>(internal, 1));
+        }
         best.nX = std::max(best.nX, w2);
-        best.ncount = std::max(best.ncount, (size_t)std::max<int64_t>(internal, 1));
     }
     return best;
 }

@@ -151,14 +151,14 @@ GBQR_API gbqr_status gbqr_autotune(gbqr_ctx *ctx, int64_t m, int64_t n, int t_la
     memset(&start, 0, sizeof start);
     start.update_prec = update_prec;
     start.cutoff_b = 16;
-    start.fanout = 8;
+    start.fanout = 0;   // the planner's adaptive fan-out
     start.lookahead = 1;
     start.fp64_gemm = GBQR_GEMM_DFMA;
     if (t_layout == GBQR_T_PANEL) start.panel_nb = (int32_t)gbqr_default_panel_nb(m, n);
 
     std::vector<Axis> axes;
     axes.push_back({&gbqr_opts::cutoff_b, {8, 16, 32, 64}});
-    axes.push_back({&gbqr_opts::fanout, {2, 4, 8}});
+    axes.push_back({&gbqr_opts::fanout, {0, 2, 4, 8, 16}});
     axes.push_back({&gbqr_opts::leaf_rows, {0, 128, 256, 512, 1024}});
     if (t_layout == GBQR_T_PANEL) {
         std::vector<int32_t> nbs;
@@ -221,12 +221,12 @@ GBQR_API gbqr_status gbqr_autotune_batched(gbqr_ctx *ctx, int count, const int64
     memset(&start, 0, sizeof start);
     start.update_prec = update_prec;
     start.cutoff_b = 16;
-    start.fanout = 8;
+    start.fanout = 0;   // the planner's adaptive fan-out
     start.batch_streams = 128;
     std::vector<Axis> axes;
     axes.push_back({&gbqr_opts::batch_streams, {16, 32, 64, 128}});
     axes.push_back({&gbqr_opts::cutoff_b, {8, 16, 32}});
-    axes.push_back({&gbqr_opts::fanout, {2, 4, 8}});
+    axes.push_back({&gbqr_opts::fanout, {0, 2, 4, 8, 16}});
     axes.push_back({&gbqr_opts::leaf_rows, {0, 256, 512}});
 
     // A batch is meant to be replayed as one captured graph (gbqr_graph_*):

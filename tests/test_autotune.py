@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def _check_candidates(gb, o, layout, prec):
     assert o.cutoff_b in (8, 16, 32, 64)
-    assert o.fanout in (2, 4, 8)
+    assert o.fanout in (0, 2, 4, 8, 16)
     assert o.leaf_rows in (0, 128, 256, 512, 1024)
     assert o.update_prec == prec
     if layout == gb.GBQR_T_PANEL:
@@ -58,7 +58,7 @@ def test_tuned_factor_is_cached_and_correct(gb, orc, layout_name):
 def test_zero_budget_keeps_the_defaults(gb):
     ctx = gb.Context(0)
     best, ms = ctx.autotune(2000, 100, gb.GBQR_T_PANEL, gb.GBQR_FP64, budget_ms=0.0)
-    assert (best.cutoff_b, best.fanout, best.leaf_rows, best.lookahead) == (16, 8, 0, 1)
+    assert (best.cutoff_b, best.fanout, best.leaf_rows, best.lookahead) == (16, 0, 0, 1)
     assert best.panel_nb == gb.default_panel_nb(2000, 100)
     assert best.fp64_gemm == gb.GBQR_GEMM_DFMA
     assert ms > 0.0
@@ -91,7 +91,7 @@ def test_tuned_batched(gb, orc):
     ctx = gb.Context(0)
     best, ms = ctx.autotune_batched(shapes, gb.GBQR_FP64, budget_ms=4000.0)
     assert best.batch_streams in (16, 32, 64, 128)
-    assert best.cutoff_b in (8, 16, 32) and best.fanout in (2, 4, 8)
+    assert best.cutoff_b in (8, 16, 32) and best.fanout in (0, 2, 4, 8, 16)
     assert ctx.tuned(gb.GBQR_TUNE_BATCHED) is not None
     mats = [workloads.gaussian(m, n, 500 + i) for i, (m, n) in enumerate(shapes)]
     As = [_gpu.device_matrix(a) for a in mats]

@@ -54,6 +54,9 @@ TUNABLES = [
     (64, 64, 0, 2),
     (64, 0, 256, 5),
     (8, 16, 33, 2),
+    (16, 0, 16, 16),   # 48 leaves: fan-out 16, two merge levels
+    (16, 0, 16, 0),    # the planner's fan-out for 48 leaves (two levels at k = 8 already)
+    (4, 0, 8, 13),
 ]
 
 
