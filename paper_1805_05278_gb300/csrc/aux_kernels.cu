@@ -299,31 +299,45 @@ __device__ void block_inverse_apply(int64_t jb, int s, const double *Di, double 
 }
 
 // Back substitution R x = c, one launch per block (from the bottom): apply
-// the just-solved block x(j0:j0+s) to rows [0, j0) - each CTA owns 256 rows -
-// then the CTA owning the block just above, rows [jn, j0), solves it.
+// the just-solved block x(j0:j0+s) to rows [0, j0) - each CTA owns 64 rows,
+// its four warp pairs splitting the block's columns in quarters (a warp reads
+// 32 consecutive rows of a column), combined in a fixed order - then the CTA
+// owning the block just above, rows [jn, j0), solves it.
 __global__ void __launch_bounds__(kThreads) trsv_step_kernel(int64_t j0, int s, int64_t jn, int sn, const double *R,
                                                            int64_t ldr, double *x, long long *rankdef,
                                                            const double *Dinv) {
+    constexpr int kRows = 64;
     __shared__ double xb[kTrsvBlock];
     __shared__ double xs[kTrsvBlock];
     __shared__ double Rs[kTrsvBlock * kTrsvBlock];
+    __shared__ double part[4][kRows];
     if (threadIdx.x < s) xb[threadIdx.x] = x[j0 + threadIdx.x];
     __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x;
-    if (i < j0 && s > 0) {
-        double acc = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-        int l = 0;
-        for (; l + 3 < s; l += 4) {
-            acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
-            a1 = fma(R[i + (j0 + l + 1) * ldr], xb[l + 1], a1);
-            a2 = fma(R[i + (j0 + l + 2) * ldr], xb[l + 2], a2);
-            a3 = fma(R[i + (j0 + l + 3) * ldr], xb[l + 3], a3);
+    const int64_t r0 = (int64_t)blockIdx.x * kRows;
+    if (s > 0) {
+        const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int q = wid >> 1, rl = (wid & 1) * 32 + lane;
+        const int64_t i = r0 + rl;
+        const int qw = (s + 3) / 4, c0 = q * qw, c1 = min(s, c0 + qw);
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        if (i < j0) {
+            const double *Ri = R + i + j0 * ldr;
+            int l = c0;
+            for (; l + 3 < c1; l += 4) {
+                a0 = fma(Ri[l * ldr], xb[l], a0);
+                a1 = fma(Ri[(l + 1) * ldr], xb[l + 1], a1);
+                a2 = fma(Ri[(l + 2) * ldr], xb[l + 2], a2);
+                a3 = fma(Ri[(l + 3) * ldr], xb[l + 3], a3);
+            }
+            for (; l < c1; ++l) a0 = fma(Ri[l * ldr], xb[l], a0);
         }
-        for (; l < s; ++l) acc = fma(R[i + (j0 + l) * ldr], xb[l], acc);
-        x[i] -= (acc + a1) + (a2 + a3);
+        part[q][rl] = (a0 + a1) + (a2 + a3);
+        __syncthreads();
+        if (threadIdx.x < kRows && r0 + threadIdx.x < j0)
+            x[r0 + threadIdx.x] -= (part[0][threadIdx.x] + part[1][threadIdx.x]) +
+                                   (part[2][threadIdx.x] + part[3][threadIdx.x]);
     }
-    const int64_t r0 = (int64_t)blockIdx.x * kThreads;
-    if (sn > 0 && jn >= r0 && jn < r0 + kThreads) {
+    if (sn > 0 && jn >= r0 && jn < r0 + kRows) {
         __syncthreads();                 // this CTA's rows [jn, j0) are final
         __threadfence_block();
         if (Dinv) {
@@ -464,7 +478,7 @@ gbqr_status trsv_upper(const Exec &ex, int64_t n, const double *R, int64_t ldr, 
         const int s = (k == nblk) ? 0 : (int)std::min<int64_t>(kTrsvBlock, n - j0);
         const int64_t jn = (k - 1) * kTrsvBlock;
         const int sn = (int)std::min<int64_t>(kTrsvBlock, n - jn);
-        const unsigned grid = (unsigned)std::max<int64_t>(1, (j0 + kThreads - 1) / kThreads);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, (j0 + 63) / 64);   // 64 rows per CTA
         trace_begin(ex, FAM_TRSV);
         trsv_step_kernel<<<grid, kThreads, 0, ex.stream>>>(j0, s, jn, sn, R, ldr, x, rankdef, Dinv);
         TRY_ST(trace_end(ex, FAM_TRSV, 2.0 * j0 * s + (double)sn * sn, 8.0 * j0 * s));
