@@ -897,10 +897,14 @@ gbqr_status gbqr::factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, 
         // PANEL with look-ahead and page-locked buffers: panels in and out on
         // the copy stream, overlapped with the factorization (factor_device)
         const HostIO io{A, lda, T, ldt};
-        TRY(factor_device(w, m, n, w.bigA, m, w.bigT, trows, t_layout, &io));
-        if (cudaStreamSynchronize(cx->copy) != cudaSuccess || cudaStreamSynchronize(cx->side) != cudaSuccess)
-            return GBQR_ECUDA;
-        return cudaStreamSynchronize(cx->stream) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
+        const gbqr_status st = factor_device(w, m, n, w.bigA, m, w.bigT, trows, t_layout, &io);
+        // drain all three streams even after an error: copies already queued
+        // still write into the caller's buffers
+        const bool ok = cudaStreamSynchronize(cx->copy) == cudaSuccess &&
+                        cudaStreamSynchronize(cx->side) == cudaSuccess &&
+                        cudaStreamSynchronize(cx->stream) == cudaSuccess;
+        if (st != GBQR_OK) return st;
+        return ok ? GBQR_OK : GBQR_ECUDA;
     }
     if (cudaMemcpy2DAsync(w.bigA, m * 8, A, lda * 8, m * 8, n, cudaMemcpyHostToDevice, cx->stream) != cudaSuccess)
         return GBQR_ECUDA;
