@@ -128,7 +128,7 @@ typedef struct {
 
 /* Per-kernel-family totals of traced launches (see gbqr_trace_enable). */
 typedef struct {
-    char name[24];         /* "gemm", "tc_gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "trsv", "gemv", "other" */
+    char name[24];         /* "gemm", "tc_gemm", "tsqr_up", "tsqr_down", "trsv", "gemv", "other" */
     int64_t launches;
     double ms;             /* summed device time between launch-bracketing events */
     double flops;          /* summed algorithmic FP64 flops of those launches */

@@ -71,7 +71,7 @@ struct EventTracer final : Tracer {
     }
 };
 
-const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "tsqr_recon", "trsv", "gemv", "other"};
+const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "trsv", "gemv", "other"};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

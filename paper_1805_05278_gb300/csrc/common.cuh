@@ -14,7 +14,7 @@ constexpr int kThreads = 256;   // threads per CTA for every kernel family
 constexpr int kMaxPanel = 64;   // largest TSQR panel width w (= cutoff b)
 
 // ---------------------------------------------------------------- tracing
-enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TSQR_RECON, FAM_TRSV, FAM_GEMV, FAM_OTHER, FAM_COUNT };
+enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TRSV, FAM_GEMV, FAM_OTHER, FAM_COUNT };
 
 struct Tracer {
     virtual void begin(cudaStream_t s, Family f) = 0;
@@ -112,7 +112,7 @@ struct TsqrPlan {
     int L = 0;          // tree levels above the leaves
     int hmax = 0;       // tallest leaf
     int ldS = 0;        // up kernel shared-memory leading dimension (>= hmax, >= k*w)
-    int ldW = 0;        // down / recon kernels shared-memory leading dimension (>= hmax)
+    int ldW = 0;        // down kernel shared-memory leading dimension (>= hmax)
     int64_t nodes = 0;  // leaves + internal nodes
     size_t smem_up = 0, smem_down = 0;
     // workspace element counts
@@ -127,7 +127,8 @@ struct TsqrWorkT {
 using TsqrWork = TsqrWorkT<double>;
 
 // Plan for an mp x w panel.  leaf_rows = target leaf height (0 = default),
-// fanout in [2, 8].  Returns false if the panel cannot be planned.
+// fanout in [2, 16], or 0: the fewest merge levels a fan-out k <= 16 gives
+// (the smallest such k >= 8).  Returns false if the panel cannot be planned.
 bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPlan *plan);
 // Worst-case plan sizes over panels of height <= mp and width <= w.
 TsqrPlan tsqr_plan_bound(int64_t mp, int w, int leaf_rows, int fanout, int num_sms);

@@ -871,7 +871,7 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     while (k > 2 && up_smem(k * w, w) > kSmemCap) --k;
     pl.k = k;
     pl.ldS = std::max(pl.hmax, pl.k * w);   // up kernel (leaf block or k stacked triangles)
-    pl.ldW = pl.hmax;                        // down / recon kernels (leaf block only)
+    pl.ldW = pl.hmax;                        // down kernel (leaf block only)
     int64_t nodes = P, Nl = P, L = 0, internal = 0;
     while (Nl > 1) { Nl = (Nl + pl.k - 1) / pl.k; nodes += Nl; internal += Nl; ++L; }
     if (L > 40) return false;
