@@ -67,6 +67,24 @@ def test_workspace_query(lib):
     assert big < 4 * 8192 * 8192 * 8
 
 
+def test_fanout_range(lib):
+    """TSQR fan-out: 0 (the planner's choice) or 2..16; anything else is an
+    invalid option.  Any valid fan-out, the widest cutoff included, gets a
+    workspace: the planner bounds it over every fan-out it may pick."""
+    import paper_1805_05278_gb300 as gb
+    for k in (0, 2, 3, 8, 13, 16):
+        for b in (16, 64):
+            o = gb.opts(fanout=k, cutoff_b=b)
+            assert gb.gbqr_workspace_bytes(32768, 2048, gb.GBQR_T_PANEL, ctypes.byref(o)) > 0, (k, b)
+    for k in (1, 17, -1):
+        o = gb.opts(fanout=k)
+        assert gb.gbqr_workspace_bytes(32768, 2048, gb.GBQR_T_PANEL, ctypes.byref(o)) == 0, k
+    # the bound over every fan-out covers the adaptive and the fixed choices
+    w0 = gb.gbqr_workspace_bytes(32768, 2048, gb.GBQR_T_PANEL, ctypes.byref(gb.opts(fanout=0)))
+    w16 = gb.gbqr_workspace_bytes(32768, 2048, gb.GBQR_T_PANEL, ctypes.byref(gb.opts(fanout=16)))
+    assert w0 == w16
+
+
 def test_default_panel(lib):
     import paper_1805_05278_gb300 as gb
     assert gb.gbqr_default_panel_nb(1000, 77) == 77
