@@ -13,9 +13,18 @@ rank factors its own matrix (independent replicas, no collective on the data
 path); the reported value is the flops of all ranks over the slowest rank's
 time.
 
---impl reference times the CPU oracle (unblocked Householder QR, one
-thread) on a bounded sample of the same workload: the first k Householder
-steps of the same matrix, credited with the flops of those k steps.
+The timed region runs with launch tracing off.  The roofline of the dominant
+kernel (the FP64 GEMM family) comes from a separate traced pass of the same
+factorization with the look-ahead off, so that every launch runs alone and
+its event-bracketed duration is its own (with look-ahead the side stream's
+panel shares the SMs and stretches the GEMMs it overlaps).
+
+--impl reference times the CPU oracle (unblocked Householder QR, the build
+whose column loops run on every host core) on a bounded, stratified sample
+of the same workload: in each of 8 equal ranges of the n Householder steps a
+few steps are timed on the trailing matrix of the range's midpoint, and the
+full factorization's time is estimated as the sum over ranges of the
+range's flops at that range's measured rate.
 """
 
 from __future__ import annotations
@@ -43,12 +52,11 @@ SM_MAX_MHZ = 2070.0
 # Derived FP64 peak: 152 SMs x 4 FP64 flop/clk/SM (2 FMA) x 2.070 GHz.
 FP64_FLOP_PER_CLK_PER_SM = 4.0
 FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-# DRAM bytes per dgemm launch (read + write, averaged over every launch of
-# one step) from an ncu capture of this exact configuration; the roofline's
-# traffic is null for any configuration without a capture.
-DGEMM_TRAFFIC_PER_LAUNCH = {
-    # (workload, panel_nb, cutoff_b, fanout, leaf_rows, lookahead, engine): bytes
-    ("graded_8192x8192", 128, 16, 8, 0, 1, "dfma"): 11.69e6,
+# DRAM bytes (read + write) of dgemm launches over their algorithmic bytes
+# 8 (MK + KN + 2MN), from an ncu capture of a few launches of this
+# configuration; the roofline's traffic is null for any other configuration.
+DGEMM_TRAFFIC_RATIO = {
+    # (workload, panel_nb, cutoff_b, engine): ratio
 }
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs peak; LS solves/s, p99 ms: mixed vs FP64"
 
@@ -61,7 +69,12 @@ def parse():
     p.add_argument("--workload", default=workloads.SQUARE_8192.name, choices=sorted(workloads.WORKLOADS))
     p.add_argument("--layout", default="panel", choices=["panel", "full"])
     p.add_argument("--impl", default="gbqr", choices=["gbqr", "reference"])
-    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample budget per oracle build")
+    p.add_argument("--roofline-steps", type=int, default=2,
+                   help="traced factorizations (look-ahead off) for the GEMM family's roofline")
+    p.add_argument("--sub-configs", default="gaussian_1024x128,graded_32768x2048",
+                   help="other workloads timed beside the headline one (library defaults)")
+    p.add_argument("--sub-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-accuracy", dest="accuracy", action="store_false",
                    help="skip the backward-error / orthogonality check after the timed region")
@@ -81,6 +94,8 @@ def parse():
     p.add_argument("--ls-solves", type=int, default=3, help="timed least-squares solves per grid point and precision (0: skip)")
     p.add_argument("--ls-decades", default="2,6,10", help="column-grading decades (kappa ~ 10^d x kappa(Gaussian))")
     p.add_argument("--ls-shapes", default="32768x2048,8192x8192")
+    p.add_argument("--ls-oracle-shapes", default="32768x2048",
+                   help="LS shapes whose results are also compared with the CPU oracle's solution")
     p.add_argument("--no-ls-kappa", action="store_true", help="skip the condition estimate (torch.linalg)")
     p.add_argument("--ls-autotune-ms", type=float, default=0.0,
                    help="gbqr_autotune budget per LS shape and precision before timing (0: defaults; the "
@@ -94,6 +109,59 @@ def parse():
     p.add_argument("--serving-rates", default="100,400,1600,5000")
     p.add_argument("--serving-workers", type=int, default=16)
     return p.parse_args()
+
+
+def accuracy_of(gb, ctx, A, T, A0, layout, nb, m, n, dev):
+    """||A - QR||_F / ||A||_F, ||Q^T Q - I||_F and ||Q^T Q - I||_2 of a
+    factorization (measurement only: torch on the device; Q from gbqr_form_q)."""
+    import torch
+    Q = gb.colmajor(m, n, f"cuda:{dev}")
+    ctx.form_q(A, T, Q, layout, nb)
+    torch.cuda.synchronize()
+    R = torch.triu(A[:n, :])
+    bwd = float(torch.linalg.matrix_norm(A0 - Q @ R) / torch.linalg.matrix_norm(A0))
+    E = Q.T @ Q
+    E.diagonal().sub_(1.0)
+    fro = float(torch.linalg.matrix_norm(E))
+    two = float(torch.linalg.eigvalsh(0.5 * (E + E.T)).abs().max())
+    del Q, R, E
+    return {"backward_err_fro": bwd, "orthogonality_fro": fro, "orthogonality_2": two}
+
+
+def measure_config(gb, dev, w, args):
+    """One other workload with the library defaults (PANEL layout): ms per
+    factorization over args.sub_steps timed steps (CUDA events, after 3
+    warm-ups, A restored from a device copy inside each step), TFLOP/s at
+    2mn^2 - 2n^3/3, and the accuracy of the last step."""
+    import torch
+    a = w.matrix()
+    A0 = gb.to_colmajor(a, f"cuda:{dev}")
+    A = gb.colmajor(w.m, w.n, f"cuda:{dev}")
+    nb = gb.default_panel_nb(w.m, w.n)
+    T = gb.colmajor(min(nb, w.n), w.n, f"cuda:{dev}")
+    stream = torch.cuda.current_stream(dev)
+    ctx = gb.Context(dev, stream)
+
+    def step():
+        A.copy_(A0)
+        ctx.factor(A, T, gb.GBQR_T_PANEL)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.sub_steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.sub_steps
+    st, _ = ctx.sync()
+    acc = accuracy_of(gb, ctx, A, T, A0, gb.GBQR_T_PANEL, nb, w.m, w.n, dev)
+    ctx.close()
+    tf = w.flops / (ms * 1e-3) / 1e12
+    return {"m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed, "ms_per_step": ms, "tflops": tf,
+            "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS, "steps": args.sub_steps, "status": int(st), **acc}
 
 
 def measure_serving(gb, dev, args):
@@ -260,6 +328,7 @@ def measure_ls(gb, ctx, dev, args):
     ctx = gb.Context(dev, stream)        # its own, library-grown workspace
     shapes = [tuple(int(v) for v in s.split("x")) for s in args.ls_shapes.split(",") if s]
     decades = [float(d) for d in str(args.ls_decades).split(",") if d]
+    oracle_shapes = set(x for x in args.ls_oracle_shapes.split(",") if x)
     grid = []
     for (m, n) in shapes:
         for d in decades:
@@ -303,6 +372,17 @@ def measure_ls(gb, ctx, dev, args):
                              "backward_err": bwd}
             row["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(xs["mixed_splitbf16"] - xs["fp64"]) /
                                                   torch.linalg.norm(xs["fp64"]))
+            if f"{m}x{n}" in oracle_shapes:
+                # both results against the FP64 oracle's solution of the same
+                # problem (all-cores build on the host; bytes copied from the device)
+                import oracle
+                t0 = time.perf_counter()
+                x_orc, _ = oracle.all_cores().ls_solve(gb.to_numpy(A), b.cpu().numpy())
+                xo = torch.from_numpy(x_orc).to(devs)
+                for name in ("fp64", "mixed_splitbf16"):
+                    row[name]["rel_err_vs_oracle"] = float(torch.linalg.norm(xs[name] - xo) / torch.linalg.norm(xo))
+                row["oracle_seconds"] = time.perf_counter() - t0
+                row["kappa_u"] = (kappa or 0.0) * 2.0 ** -53
             row["speedup_mixed"] = row["mixed_splitbf16"]["solves_per_s"] / row["fp64"]["solves_per_s"]
             grid.append(row)
             del A, b, xt
@@ -391,22 +471,83 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU baseline
-def oracle_sample(a: np.ndarray, budget_s: float):
-    """Times the oracle on the first k Householder steps of a, with k sized so
-    that the run takes about budget_s seconds; returns (tflops, k, seconds)."""
-    import oracle
-    orc = oracle.default()
-    m, n = a.shape
-    k0 = max(1, min(n, 2))
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else platform)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _oracle_steps_seconds(orc, block: np.ndarray, k: int) -> float:
+    """Seconds of the oracle's C call for the first k Householder steps of a
+    fresh copy of block (the copy is made outside the timed call)."""
+    import ctypes
+    work = np.array(block, dtype=np.float64, order="F", copy=True)
+    mm, nn = work.shape
+    tau = np.zeros(max(1, min(mm, nn)))
+    P = ctypes.POINTER(ctypes.c_double)
     t0 = time.perf_counter()
-    orc.house_qr(a, nsteps=k0)
-    t1 = time.perf_counter() - t0
-    per_step = t1 / k0
-    k = int(max(1, min(n, budget_s / max(per_step, 1e-9))))
-    t0 = time.perf_counter()
-    orc.house_qr(a, nsteps=k)
+    rc = orc.lib.orc_house_qr(mm, nn, work.ctypes.data_as(P), max(1, mm), tau.ctypes.data_as(P), k)
     dt = time.perf_counter() - t0
-    return workloads.qr_flops_partial(m, n, k) / dt / 1e12, k, dt
+    if rc != 0:
+        raise RuntimeError(f"oracle house_qr returned {rc}")
+    return dt
+
+
+def oracle_rate(orc, a: np.ndarray, budget_s: float, strata: int = 8):
+    """Stratified estimate of the oracle's rate on the full QR of a.  The n
+    Householder steps are cut into `strata` equal ranges; in each, k steps
+    (sized to budget_s / strata seconds) are timed on the trailing matrix at
+    the range's middle, and the range's time is its flops at that rate.
+    Returns (TFLOP/s of the whole factorization, estimated seconds for it,
+    sampled steps, seconds spent in the sampled calls)."""
+    m, n = a.shape
+    kmax = min(m, n)
+    bounds = [round(s * kmax / strata) for s in range(strata + 1)]
+    per = budget_s / strata
+    est, steps, spent = 0.0, 0, 0.0
+    for s in range(strata):
+        j0, j1 = bounds[s], bounds[s + 1]
+        if j1 <= j0:
+            continue
+        mid = (j0 + j1) // 2
+        t1 = _oracle_steps_seconds(orc, a[mid:, mid:], 1)
+        k = int(max(1, min(j1 - j0, per / max(t1, 1e-9))))
+        start = max(j0, min(mid - k // 2, j1 - k))
+        tk = _oracle_steps_seconds(orc, a[start:, start:], k)
+        rate = workloads.qr_flops_partial(m - start, n - start, k) / max(tk, 1e-12)
+        est += workloads.qr_flops_partial(m - j0, n - j0, j1 - j0) / rate
+        steps += k
+        spent += t1 + tk
+    return workloads.qr_flops(m, n) / est / 1e12, est, steps, spent
+
+
+def cpu_baseline(a: np.ndarray, budget_s: float) -> dict:
+    """The oracle on this host: the all-cores build (reported value) and the
+    one-thread build, each a stratified sample of budget_s seconds."""
+    import oracle
+    par, ser = oracle.all_cores(), oracle.default()
+    tf, est, steps, spent = oracle_rate(par, a, budget_s)
+    tf1, est1, steps1, spent1 = oracle_rate(ser, a, budget_s)
+    m, n = a.shape
+    return {"value": tf, "unit": "TFLOP/s", "cores": par.threads, "kind": "oracle",
+            "sample": f"stratified: {steps} of {min(m, n)} Householder steps of the same {m}x{n} matrix, "
+                      f"8 step ranges, each timed at its midpoint ({spent:.1f} s); full QR estimated at {est:.1f} s",
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(), "build": "oracle/house.c -fopenmp (all cores)",
+            "single_thread": {"value": tf1, "unit": "TFLOP/s", "cores": 1, "estimated_full_qr_s": est1,
+                              "sample": f"{steps1} steps ({spent1:.1f} s), same strata"}}
 
 
 def run_reference(args):
@@ -415,31 +556,31 @@ def run_reference(args):
         return 0
     w = workloads.WORKLOADS[args.workload]
     a = w.matrix()
-    # each step: a bounded sample (first k Householder steps) of the workload
-    per_step_budget = max(0.5, min(4.0, 150.0 / max(1, args.steps + args.warmup)))
+    # each step: one stratified sample of the workload, sized so that the
+    # whole run ends within a few minutes
+    per_step_budget = max(0.8, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
     import oracle
-    orc = oracle.default()
-    t0 = time.perf_counter()
-    orc.house_qr(a, nsteps=2)
-    per = (time.perf_counter() - t0) / 2
-    k = int(max(1, min(w.n, per_step_budget / max(per, 1e-9))))
+    orc = oracle.all_cores()
     for _ in range(args.warmup):
-        orc.house_qr(a, nsteps=k)
-    times = []
+        oracle_rate(orc, a, per_step_budget)
+    ests, spent, steps = [], 0.0, 0
     for _ in range(args.steps):
-        t0 = time.perf_counter()
-        orc.house_qr(a, nsteps=k)
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    flops = workloads.qr_flops_partial(w.m, w.n, k) * args.steps
-    value = flops / total / 1e12
-    sample = f"first {k} of {w.n} Householder steps of the {w.m}x{w.n} matrix per step, single thread"
+        _, est, k, sp = oracle_rate(orc, a, per_step_budget)
+        ests.append(est)
+        spent += sp
+        steps += k
+    est_mean = sum(ests) / len(ests)
+    value = w.flops / est_mean / 1e12
+    sample = (f"per step: a stratified sample of the {w.m}x{w.n} factorization (8 step ranges, a few steps timed "
+              f"at each range's midpoint; {steps} steps, {spent:.1f} s over {args.steps} steps), the full "
+              f"factorization's time estimated from it; oracle built with OpenMP on {orc.threads} threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * est_mean,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "m": w.m, "n": w.n, "graded": w.graded, "seed": w.seed},
-        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": orc.threads, "kind": "oracle",
+                         "sample": sample, "nproc": os.cpu_count(), "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -502,9 +643,7 @@ def run_gbqr(args):
     if st != gb.GBQR_OK:
         raise RuntimeError(f"warm-up reported status {st}")
 
-    # timed region: K steps with launch tracing on, clocks sampled alongside
-    ctx.trace(True)
-    ctx.trace_read()
+    # timed region: K steps, launch tracing off, clocks sampled alongside
     launches0 = ctx.launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist:
@@ -519,12 +658,28 @@ def run_gbqr(args):
     if dist:
         dist.barrier()
     ms_total = ev0.elapsed_time(ev1)
-    trace = ctx.trace_read()
-    ctx.trace(False)
     launches = ctx.launch_count() - launches0
     clocks = clk.summary()
     ms_step = max_over_ranks(ms_total / args.steps, dist, f"cuda:{dev}")
     value = whole_job_tflops(w.flops, world, ms_step)
+
+    # roofline pass (after the timed region): the same factorization with the
+    # look-ahead off, traced, so that each launch runs alone on the GPU and
+    # its event-bracketed duration is its own; the GEMM family's summed time
+    # then cannot exceed the step's
+    o_serial = gb.opts(**{**gb.opts_dict(o), "lookahead": -1})
+    ctx.trace(True)
+    ctx.trace_read()
+    es0, es1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    es0.record(stream)
+    for _ in range(args.roofline_steps):
+        A.copy_(A0)
+        ctx.factor(A, T, layout, o_serial)
+    es1.record(stream)
+    torch.cuda.synchronize()
+    serial_ms = es0.elapsed_time(es1)
+    trace = ctx.trace_read()
+    ctx.trace(False)
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     a_pin = torch.from_numpy(np.ascontiguousarray(a_host.T)).pin_memory()   # (n, m) row-major = A column-major
@@ -545,16 +700,10 @@ def run_gbqr(args):
     accuracy = None
     if args.accuracy and w.m >= w.n:
         try:
-            Q = gb.colmajor(w.m, w.n, f"cuda:{dev}")
-            ctx.form_q(A, T, Q, layout, nb)
+            step()                      # one more factorization in the timed configuration
             torch.cuda.synchronize()
-            R = torch.triu(A[:w.n, :])
-            bwd = float(torch.linalg.matrix_norm(A0 - Q @ R) / torch.linalg.matrix_norm(A0))
-            QtQ = Q.T @ Q
-            QtQ.diagonal().sub_(1.0)
-            accuracy = {"backward_err_fro": bwd, "orthogonality_fro": float(torch.linalg.matrix_norm(QtQ)),
-                        "note": "||A - QR||_F / ||A||_F and ||Q^T Q - I||_F of the last timed step, FP64"}
-            del Q, R, QtQ
+            accuracy = accuracy_of(gb, ctx, A, T, A0, layout, nb, w.m, w.n, dev)
+            accuracy["note"] = "||A - QR||_F / ||A||_F, ||Q^T Q - I||_F and _2 of a step in the timed configuration, FP64"
         except (gb.GbqrError, RuntimeError) as exc:
             accuracy = {"error": str(exc)}
 
@@ -565,27 +714,42 @@ def run_gbqr(args):
 
     gemm = trace.get("gemm", {})
     achieved = gemm["flops"] / (gemm["ms"] * 1e-3) / 1e12 if gemm.get("ms") else None
+    share = (gemm.get("ms", 0.0) / serial_ms) if serial_ms else None
+    if share is not None and share > 1.0:
+        raise RuntimeError(f"GEMM family time exceeds the step in the serial pass (share {share:.3f})")
+    alg_bytes = (gemm["bytes"] / gemm["launches"]) if gemm.get("launches") else None
+    ratio = DGEMM_TRAFFIC_RATIO.get(
+        (w.name, nb if layout == gb.GBQR_T_PANEL else 0, o.cutoff_b or 16, "dmma" if o.fp64_gemm == gb.GBQR_GEMM_DMMA else "dfma"))
     roofline = {
         "bound": "alu", "kernel": "dgemm_kernel (update / T-assembly products)",
         "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
         "frac": (achieved / FP64_PEAK_TFLOPS) if achieved else None,
-        "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.070 GHz (nominal 1.25 TFLOP/s FP64)",
-        "traffic": DGEMM_TRAFFIC_PER_LAUNCH.get(
-            (w.name, nb if layout == gb.GBQR_T_PANEL else 0, o.cutoff_b or 16, o.fanout or 8, o.leaf_rows,
-             o.lookahead or 1, "dmma" if o.fp64_gemm == gb.GBQR_GEMM_DMMA else "dfma")),
-        "traffic_unit": "bytes per launch (dram read + write, ncu)",
-        "algorithmic_bytes_per_launch": (gemm["bytes"] / gemm["launches"]) if gemm.get("launches") else None,
-        "launches": gemm.get("launches"), "share_of_step": (gemm.get("ms", 0.0) / ms_total) if ms_total else None,
+        "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.070 GHz (nominal 1.25 TFLOP/s FP64); "
+                       "measured DFMA probe 1.06, DMMA probe 1.10, largest update launch 1.22 TFLOP/s",
+        "how": f"algorithmic flops / summed CUDA-event durations of every GEMM launch in {args.roofline_steps} "
+               f"traced factorizations with the look-ahead off (launches run alone)",
+        "traffic": (ratio * alg_bytes) if (ratio and alg_bytes) else None,
+        "traffic_unit": "bytes per launch (dram read + write): ncu ratio to algorithmic bytes x this pass's "
+                        "algorithmic bytes per launch",
+        "traffic_ratio_ncu": ratio,
+        "algorithmic_bytes_per_launch": alg_bytes,
+        "launches": gemm.get("launches"), "share_of_step": share,
+        "serial_ms_per_step": serial_ms / max(1, args.roofline_steps),
+        "step_frac": value / world / FP64_PEAK_TFLOPS,
     }
-    fams = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                "algorithmic_bytes_per_step": v["bytes"] / args.steps,
+    fams = {k: {"launches": v["launches"] / max(1, args.roofline_steps),
+                "ms_per_step": v["ms"] / max(1, args.roofline_steps),
+                "algorithmic_bytes_per_step": v["bytes"] / max(1, args.roofline_steps),
                 "tflops": (v["flops"] / (v["ms"] * 1e-3) / 1e12) if v["ms"] else None} for k, v in trace.items()}
+
+    subs = {}
+    if rank == 0 and args.sub_configs:
+        for name in [n_ for n_ in args.sub_configs.split(",") if n_]:
+            subs[name] = measure_config(gb, dev, workloads.WORKLOADS[name], args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        tf, k, dt = oracle_sample(a_host, args.cpu_seconds)
-        cpu = {"value": tf, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {k} of {w.n} Householder steps of the same {w.m}x{w.n} matrix ({dt:.1f} s, single thread)"}
+        cpu = cpu_baseline(a_host, args.cpu_seconds)
 
     if rank == 0:
         line = {
@@ -604,7 +768,8 @@ def run_gbqr(args):
                     "how": "gbqr_factor on pinned host buffers (H2D, factor, D2H inside the call)"},
             "gpu_launches": launches,
             "roofline": roofline,
-            "families": fams,
+            "families_serial_pass": fams,
+            "configs": subs,
             "clocks": clocks,
             "cpu_baseline": cpu,
             "ls": ls,

@@ -398,17 +398,22 @@ typedef struct {
     double queue_ms;       /* submit -> admitted */
     double run_ms;         /* admitted -> done */
     double latency_ms;     /* submit -> done */
-    int64_t footprint_bytes;
+    int64_t footprint_bytes; /* workspace + the request's A, b, x bytes, held against the cap */
     uint64_t tag;
+    int32_t bypassed;      /* later requests admitted while this one waited (<= 8) */
+    int32_t pad2;
 } gbqr_result;
 
 /* Start a serving loop on `device` attached to ctx: `workers` host threads,
  * each with a private context and stream, so admitted requests overlap on
- * the device; at most mem_cap_bytes of workspace in flight.  A queued request
- * is admitted (first fit, in arrival order) when a worker is free and its
- * workspace footprint - gbqr_workspace_bytes of its shape and precision -
- * fits under the cap beside the running ones; its workspace comes from the
- * stream-ordered allocator and returns on completion.  Each request runs
+ * the device; at most mem_cap_bytes of request footprint in flight.  A
+ * request's footprint is its workspace (gbqr_workspace_bytes of its shape
+ * and precision, + 1 MiB) plus its own A, b and x.  A queued request is
+ * admitted (first fit, in arrival order) when a worker is free and its
+ * footprint fits under the cap beside the running ones; at most 8 later
+ * requests may be admitted ahead of a waiting one, after which it blocks the
+ * queue until it fits (at the latest when nothing else runs).  Its workspace
+ * comes from the stream-ordered allocator and returns on completion.  Each request runs
  * gbqr_ls_solve (Section 2.1 least squares through the QR); the kernels are
  * deterministic, so a result does not depend on what else is in flight.
  * Errors: EINVAL, EBUSY (already started), ENOMEM, ECUDA. */
@@ -455,14 +460,20 @@ GBQR_API int64_t gbqr_launch_count(const gbqr_ctx *ctx);
  *   T (n x n, ldt >= n): out: the n x n upper triangular kernel, zeros below.
  *   cuda_stream:         the cudaStream_t to enqueue on (asynchronous).
  * Every GPU that loads this library holds the 16 MiB array until the
- * process exits.  All calls share it and it keeps the last call's contents;
- * each call clears the tree's arrival counters itself.  Calls that overlap on
- * the GPU (other streams, other host threads) race on the array: serialise
- * them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Sizes whose reduction tree does not fit the
- * array (leaves grown up to the shared-memory limit first), n > 32, m < n or
- * too small leading dimensions return EINVAL before any CUDA call.
+ * process exits.  Under lazy module loading (CUDA_MODULE_LOADING=LAZY, the
+ * default) the array comes into being on a device at the first call there,
+ * which may therefore allocate and synchronise; under EAGER loading it exists
+ * from context creation.  Make that first call at initialisation, and before
+ * any stream capture: it also looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current).  All calls share the
+ * array and it keeps the last call's contents; each call clears the tree's
+ * arrival counters itself.  Calls that overlap on the GPU (other streams,
+ * other host threads) race on the array: serialise them.  The tree is the one
+ * gbqr_factor plans for an m x n base case (default leaf height, adaptive
+ * fan-out).  Leaves are at most about 600 rows tall (shared memory) at
+ * n = 32, so the array holds the tree of m up to about 400,000 rows there.
+ * Larger m, n > 32, m < n or too small leading dimensions return EINVAL
+ * before any CUDA call.
  * Errors: EINVAL, ECUDA, EUNSUPPORTED (device index >= 64). */
 GBQR_API gbqr_status gbqr_tsqr_static(int64_t m, int64_t n, double *A, int64_t lda,
                                       double *T, int64_t ldt, void *cuda_stream);
@@ -485,13 +496,6 @@ GBQR_API gbqr_status gbqr_fp64_peak(int device, int kind, int iters, double *tfl
  * The paper has no counterpart.  Synchronous (about 2 s); allocates 8 bytes.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 GBQR_API gbqr_status gbqr_selftest_wait_timeout(int device, int *completed);
-
-/* Cycles per dependent FP64 operation of a warp when `warps` warps (1..32)
- * of one CTA run such chains at once: op 0 = FMA, 1 = sqrt, 2 = reciprocal
- * (each with an add).  The paper has no counterpart: it measures the issue
- * cost that bounds the latency-bound steps (reflector generation).
- * Synchronous; allocates 8.3 KB.  Errors: EINVAL, ENOMEM, ECUDA. */
-GBQR_API gbqr_status gbqr_fp64_issue_cycles(int device, int op, int warps, double *cycles);
 
 /* Human-readable name of a status. */
 GBQR_API const char *gbqr_strerror(gbqr_status s);

@@ -22,23 +22,35 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCE = os.path.join(_HERE, "house.c")
 BUILD_DIR = os.path.join(_HERE, "_build")
 LIBRARY = os.path.join(BUILD_DIR, "liboracle.so")
+LIBRARY_OMP = os.path.join(BUILD_DIR, "liboracle_omp.so")
 
 _lock = threading.Lock()
 _default = None
+_all_cores = None
 
 
-def build(source: str = SOURCE, out: str = LIBRARY, force: bool = False) -> str:
+def build(source: str = SOURCE, out: str | None = None, force: bool = False, openmp: bool = False) -> str:
     """Compile ``source`` into the shared library ``out`` (gcc, no FMA
-    contraction so that x86 and Arm hosts round identically)."""
+    contraction so that x86 and Arm hosts round identically).  openmp: the
+    all-cores build of the same source (-fopenmp), whose results are
+    bit-identical to the plain build's."""
+    if out is None:
+        out = LIBRARY_OMP if openmp else LIBRARY
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(source):
         return out
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-o", tmp, source, "-lm"]
+           *(["-fopenmp"] if openmp else []), "-o", tmp, source, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
+
+
+def build_all(force: bool = False) -> None:
+    """Both builds of the oracle: one thread and all cores."""
+    build(force=force)
+    build(force=force, openmp=True)
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -72,8 +84,15 @@ class Oracle:
             f = getattr(lib, name)
             f.argtypes = args
             f.restype = ctypes.c_int
+        lib.orc_threads.argtypes = []
+        lib.orc_threads.restype = ctypes.c_int
         self.lib = lib
         self.path = path
+
+    @property
+    def threads(self) -> int:
+        """Threads the all-cores build shares its loops over (1 for the plain build)."""
+        return int(self.lib.orc_threads())
 
     @staticmethod
     def _check(rc: int, name: str):
@@ -178,9 +197,20 @@ def sign_normalise(r: np.ndarray, q: np.ndarray | None = None):
 
 
 def default() -> Oracle:
-    """The oracle built from ``house.c`` (compiled on first use)."""
+    """The oracle built from ``house.c`` (compiled on first use), one thread."""
     global _default
     with _lock:
         if _default is None:
             _default = Oracle(build())
         return _default
+
+
+def all_cores() -> Oracle:
+    """The OpenMP build of the same ``house.c``: its column loops run on every
+    core (OMP_NUM_THREADS caps them); results equal the plain build's bit for
+    bit."""
+    global _all_cores
+    with _lock:
+        if _all_cores is None:
+            _all_cores = Oracle(build(openmp=True))
+        return _all_cores

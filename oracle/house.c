@@ -40,12 +40,22 @@
  *    solution x = R^{-1} (Q^T b)(0:n) of min ||A x - b|| (m >= n, Section 2.1).
  *
  * Nothing here is blocked, fused or reordered beyond those definitions.
+ *
+ * Built twice: plain (one thread) and with -fopenmp (all cores).  The OpenMP
+ * pragmas only share out loops whose iterations write disjoint columns
+ * (the columns that one reflector updates, the columns one reflector is
+ * applied to, the entries of one column of T); each iteration's own
+ * arithmetic and its order are unchanged, so both builds give bit-identical
+ * results.
  */
 
 #include <math.h>
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define AT(a, i, j, ld) ((a)[(size_t)(i) + (size_t)(j) * (size_t)(ld)])
 
@@ -96,6 +106,7 @@ int orc_house_qr(long m, long n, double *a, long lda, double *tau, long nsteps)
             AT(a, j, j, lda) = beta;
         }
         /* apply H_j = I - tau_j v v^T to A(j:m, j+1:n), v = [1; A(j+1:m, j)] */
+#pragma omp parallel for schedule(static) if (m * (n - j) > 65536)
         for (long c = j + 1; c < n; ++c) {
             double w = AT(a, j, c, lda);
             for (long r = j + 1; r < m; ++r) w += AT(a, r, j, lda) * AT(a, r, c, lda);
@@ -124,7 +135,9 @@ int orc_larft(long m, long n, const double *v, long ldv, const double *tau, doub
     if (!z) return 2;
     for (long j = 0; j < n; ++j) {
         for (long i = 0; i < n; ++i) AT(t, i, j, ldt) = 0.0;
+#pragma omp parallel for schedule(static) if (m * j > 65536)
         for (long i = 0; i < j; ++i) z[i] = vdot(m, v, ldv, i, j);
+#pragma omp parallel for schedule(static) if (j * j > 65536)
         for (long i = 0; i < j; ++i) {
             double s = 0.0;
             for (long k = i; k < j; ++k) s += AT(t, i, k, ldt) * z[k];
@@ -168,6 +181,7 @@ int orc_t_from_gram(long m, long n, const double *v, long ldv, double *t, long l
 static void apply_reflector(long m, long j, const double *v, long ldv, double tauj,
                             long nrhs, double *b, long ldb)
 {
+#pragma omp parallel for schedule(static) if (m * nrhs > 65536)
     for (long c = 0; c < nrhs; ++c) {
         double w = AT(b, j, c, ldb);
         for (long r = j + 1; r < m; ++r) w += AT(v, r, j, ldv) * AT(b, r, c, ldb);
@@ -238,4 +252,15 @@ int orc_ls_solve(long m, long n, const double *a, long lda, const double *b,
     }
     free(w); free(tau); free(c);
     return rc;
+}
+
+/* Threads the loops above share out: omp_get_max_threads() in the OpenMP
+ * build, 1 in the plain one. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }

@@ -59,7 +59,7 @@ class gbqr_result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("prec_used", ctypes.c_int32),
                 ("fell_back", ctypes.c_int32), ("refine_iters", ctypes.c_int64), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double), ("footprint_bytes", ctypes.c_int64),
-                ("tag", ctypes.c_uint64)]
+                ("tag", ctypes.c_uint64), ("bypassed", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
 
 class gbqr_trace_rec(ctypes.Structure):
@@ -111,7 +111,6 @@ SIGNATURES = {
     "gbqr_tuned_lookup": (ctypes.c_int, [_P, ctypes.c_int, _I64, _I64, ctypes.c_int, ctypes.c_int,
                                          ctypes.POINTER(gbqr_opts)]),
     "gbqr_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
-    "gbqr_fp64_issue_cycles": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gbqr_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
@@ -433,14 +432,6 @@ def fp64_peak(device: int = 0, kind: int = 0, iters: int = 20000) -> float:
     load()
     out = ctypes.c_double(0.0)
     check(gbqr_fp64_peak(device, kind, iters, ctypes.byref(out)), "gbqr_fp64_peak")  # noqa: F821
-    return out.value
-
-
-def fp64_issue_cycles(device: int = 0, op: int = 0, warps: int = 1) -> float:
-    """Cycles per dependent FP64 op per warp (op 0 FMA, 1 sqrt, 2 reciprocal)."""
-    load()
-    out = ctypes.c_double(0.0)
-    check(gbqr_fp64_issue_cycles(device, op, warps, ctypes.byref(out)), "gbqr_fp64_issue_cycles")  # noqa: F821
     return out.value
 
 

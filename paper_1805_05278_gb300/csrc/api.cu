@@ -900,9 +900,10 @@ gbqr_status gbqr::factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, 
         const gbqr_status st = factor_device(w, m, n, w.bigA, m, w.bigT, trows, t_layout, &io);
         // drain all three streams even after an error: copies already queued
         // still write into the caller's buffers
-        const bool ok = cudaStreamSynchronize(cx->copy) == cudaSuccess &&
-                        cudaStreamSynchronize(cx->side) == cudaSuccess &&
-                        cudaStreamSynchronize(cx->stream) == cudaSuccess;
+        const cudaError_t e_copy = cudaStreamSynchronize(cx->copy);
+        const cudaError_t e_side = cudaStreamSynchronize(cx->side);
+        const cudaError_t e_main = cudaStreamSynchronize(cx->stream);
+        const bool ok = e_copy == cudaSuccess && e_side == cudaSuccess && e_main == cudaSuccess;
         if (st != GBQR_OK) return st;
         return ok ? GBQR_OK : GBQR_ECUDA;
     }

@@ -11,7 +11,10 @@
 //
 // The array below is part of the module image: every GPU that loads this
 // library holds kStaticScratchBytes of device memory for it until the
-// process exits.  All calls share it and it keeps the last call's contents,
+// process exits.  With lazy module loading (CUDA's default) the module, and
+// with it the array, is loaded on a device by the first call there, which may
+// then allocate and synchronise; callers that must avoid that make one call
+// at initialisation.  All calls share it and it keeps the last call's contents,
 // so each call clears the part that must start at zero (the tree's arrival
 // counters).  Calls that overlap on the GPU (different streams, or different
 // host threads) race on the array.
@@ -43,19 +46,18 @@ size_t scratch_bytes(const gbqr::TsqrPlan &pl) {
            align256(pl.ncount * 4);
 }
 
-// Smallest leaf-height target (doubling from the default) whose tree fits.
+// The base case's own plan: default leaf height and the adaptive fan-out of
+// gbqr_factor.  No other plan needs less scratch: the default already takes
+// the fewest leaves the kernels' shared memory allows once a panel needs more
+// than one leaf per SM (leaf height is capped at about 600 rows at n = 32),
+// and fewer leaves means fewer tree nodes.  With n = 32 the 16 MiB hold
+// about 650 leaves, so m up to about 400,000 rows.
 bool plan_that_fits(int64_t m, int n, gbqr::TsqrPlan *out) {
-    // leaves can never be taller than 2^20 rows (shared memory), so the
-    // doubling stops there
-    int64_t target = 0;
-    for (;;) {
-        gbqr::TsqrPlan pl;
-        if (!gbqr::tsqr_plan(m, n, (int)target, 2, 0, &pl)) return false;
-        if (scratch_bytes(pl) <= kStaticScratchBytes) { *out = pl; return true; }
-        const int64_t next = target ? 2 * target : 128;
-        if (next > std::min<int64_t>(m, 1 << 20) || pl.P == 1) return false;
-        target = next;
-    }
+    gbqr::TsqrPlan pl;
+    if (!gbqr::tsqr_plan(m, n, 0, 0, 0, &pl)) return false;
+    if (scratch_bytes(pl) > kStaticScratchBytes) return false;
+    *out = pl;
+    return true;
 }
 
 }  // namespace

@@ -44,53 +44,10 @@ __global__ void __launch_bounds__(kThreads) dmma_probe_kernel(int iters, double 
     if (s == 12345.678) out[0] = s;
 }
 
-// One CTA of `warps` warps, each running a chain of dependent FP64
-// operations; clock64 per warp.  op 0: DFMA, 1: sqrt, 2: reciprocal.
-constexpr int kLatIters = 256;
-
-__global__ void latency_probe_kernel(int op, double *out, long long *cyc) {
-    double x = 1.0 + threadIdx.x * 1e-9;
-    const double a = 0.9999999, b = 1e-7;
-    __syncthreads();
-    const long long t0 = clock64();
-    for (int i = 0; i < kLatIters; ++i) {
-        if (op == 0) x = fma(x, a, b);
-        else if (op == 1) x = sqrt(x + b);
-        else x = 1.0 / (x + b);
-    }
-    const long long t1 = clock64();
-    out[threadIdx.x] = x;
-    if ((threadIdx.x & 31) == 0) cyc[threadIdx.x >> 5] = t1 - t0;
-}
-
 }  // namespace
 }  // namespace gbqr
 
 struct gbqr_ctx;
-
-extern "C" GBQR_API gbqr_status gbqr_fp64_issue_cycles(int device, int op, int warps, double *cycles) {
-    using namespace gbqr;
-    if (!cycles || op < 0 || op > 2 || warps < 1 || warps > 32) return GBQR_EINVAL;
-    if (cudaSetDevice(device) != cudaSuccess) return GBQR_ECUDA;
-    double *out = nullptr;
-    long long *cyc = nullptr;
-    if (cudaMalloc(&out, 1024 * sizeof(double)) != cudaSuccess) return GBQR_ENOMEM;
-    if (cudaMalloc(&cyc, 32 * sizeof(long long)) != cudaSuccess) { cudaFree(out); return GBQR_ENOMEM; }
-    long long h[32] = {0};
-    gbqr_status st = GBQR_OK;
-    for (int rep = 0; rep < 2 && st == GBQR_OK; ++rep) {
-        latency_probe_kernel<<<1, warps * 32>>>(op, out, cyc);
-        if (cudaDeviceSynchronize() != cudaSuccess) st = GBQR_ECUDA;
-    }
-    if (st == GBQR_OK && cudaMemcpy(h, cyc, warps * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
-        st = GBQR_ECUDA;
-    long long mx = 0;
-    for (int i = 0; i < warps; ++i) mx = h[i] > mx ? h[i] : mx;
-    *cycles = (double)mx / kLatIters;
-    cudaFree(out);
-    cudaFree(cyc);
-    return st;
-}
 
 extern "C" GBQR_API gbqr_status gbqr_fp64_peak(int device, int kind, int iters, double *tflops) {
     using namespace gbqr;

@@ -3,10 +3,13 @@
 // Requests are queued by gbqr_submit and served by W worker threads, each
 // owning a private context (its own CUDA stream), so the device overlaps the
 // work of every admitted request.  Admission is by HBM footprint: a request
-// starts when a worker is idle and its workspace (gbqr_workspace_bytes for
-// its shape and precision) fits under the byte cap together with the
-// requests already running; the queue is scanned first-fit, so a small
-// request can start while a large one waits for memory.  Each request's
+// starts when a worker is idle and its footprint (its workspace,
+// gbqr_workspace_bytes for its shape and precision, plus its own A, b and x)
+// fits under the byte cap together with the requests already running; the queue is scanned first-fit, so a small
+// request can start while a large one waits for memory - but at most
+// kMaxBypass later requests may start ahead of a waiting one: after that it
+// blocks the queue until it fits (at the latest when nothing else runs), so
+// no request waits indefinitely behind a stream of small ones.  Each request's
 // workspace comes from the stream-ordered allocator and is returned when it
 // completes, so memory freed by one request admits the next.
 //
@@ -30,9 +33,13 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Later requests that may be admitted ahead of a waiting one.
+constexpr int kMaxBypass = 8;
+
 struct Record {
     gbqr_request req;
     size_t footprint = 0;
+    int bypassed = 0;      // later requests admitted while this one waited
     int state = GBQR_REQ_QUEUED;
     gbqr_status status = GBQR_OK;
     int prec_used = GBQR_FP64;
@@ -51,9 +58,15 @@ int auto_precision(int64_t m, int64_t n) {
     return (n >= 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
 }
 
-// Workspace of gbqr_ls_solve for this request: its shape and precision, with
-// the serving context's autotuned parameters where it has some (the workers
-// carry a copy of that cache, so they size their work the same way).
+// The request's own device operands: A (lda x n), b (m) and x (n), FP64.
+size_t operand_bytes(const gbqr_request &r) {
+    return sizeof(double) * ((size_t)r.lda * (size_t)r.n + (size_t)r.m + (size_t)r.n);
+}
+
+// HBM a request holds while it runs: the workspace of gbqr_ls_solve for its
+// shape and precision (with the serving context's autotuned parameters where
+// it has some - the workers carry a copy of that cache, so they size their
+// work the same way), plus its own A (lda x n), b (m) and x (n).
 size_t footprint_of(const gbqr_ctx *cx, const gbqr_request &r, int prec) {
     gbqr_opts o;
     memset(&o, 0, sizeof o);
@@ -61,7 +74,7 @@ size_t footprint_of(const gbqr_ctx *cx, const gbqr_request &r, int prec) {
         o.batch_streams = 0;
     }
     o.update_prec = prec;
-    return gbqr_workspace_bytes(r.m, r.n, GBQR_T_PANEL, &o) + ((size_t)1 << 20);
+    return gbqr_workspace_bytes(r.m, r.n, GBQR_T_PANEL, &o) + ((size_t)1 << 20) + operand_bytes(r);
 }
 
 }  // namespace
@@ -94,13 +107,17 @@ void worker_loop(gbqr_server *sv, int wi) {
             std::unique_lock<std::mutex> lk(sv->mu);
             for (;;) {
                 if (sv->stopping && sv->queue.empty()) return;
-                // first request (in arrival order) whose footprint fits
+                // first request (in arrival order) whose footprint fits; a
+                // request already passed kMaxBypass times stops the scan, so
+                // nothing behind it starts before it does
                 auto it = sv->queue.begin();
                 for (; it != sv->queue.end(); ++it) {
                     Record &r = sv->recs[*it];
                     if (sv->in_use + r.footprint <= sv->cap || sv->running == 0) break;
+                    if (r.bypassed >= kMaxBypass) { it = sv->queue.end(); break; }
                 }
                 if (it != sv->queue.end()) {
+                    for (auto jt = sv->queue.begin(); jt != it; ++jt) ++sv->recs[*jt].bypassed;
                     id = *it;
                     sv->queue.erase(it);
                     rec = &sv->recs[id];
@@ -120,11 +137,12 @@ void worker_loop(gbqr_server *sv, int wi) {
         int used = r.prec;
         bool fell_back = false;
         void *ws = nullptr;
-        if (cudaMallocAsync(&ws, rec->footprint, st) != cudaSuccess) {
+        const size_t ws_bytes = rec->footprint - operand_bytes(r);   // the rest is the caller's A, b, x
+        if (cudaMallocAsync(&ws, ws_bytes, st) != cudaSuccess) {
             cudaGetLastError();
             status = GBQR_ENOMEM;
         } else {
-            gbqr_set_workspace(cx, ws, rec->footprint);
+            gbqr_set_workspace(cx, ws, ws_bytes);
             gbqr_info info;
             const int first = (r.prec == GBQR_PREC_AUTO) ? auto_precision(r.m, r.n) : r.prec;
             used = first;
@@ -258,6 +276,7 @@ GBQR_API gbqr_status gbqr_poll(gbqr_ctx *ctx, uint64_t id, int wait, gbqr_result
         out->run_ms = ms_between(r.t_start, r.t_done);
         out->latency_ms = ms_between(r.t_submit, r.t_done);
         out->footprint_bytes = (int64_t)r.footprint;
+        out->bypassed = r.bypassed;
         sv->recs.erase(it);   // results are read once
     }
     return GBQR_OK;

@@ -95,3 +95,42 @@ def test_invalid_requests_are_rejected(gb):
         ctx.submit(big, bb, xb, gb.GBQR_FP64)             # footprint above the 64 MiB cap
     ctx.stop_serving()
     ctx.close()
+
+
+def test_bounded_bypass_of_a_large_request(gb, orc):
+    """A large request that only fits alone, queued behind running requests
+    and ahead of a stream of small ones: first-fit lets small ones pass it,
+    but at most 8 of them (its result reports how many did), after which it
+    blocks the queue until it fits - so it cannot wait indefinitely."""
+    import torch
+    ctx = gb.Context(0)
+
+    def footprint(m, n):
+        return gb.workspace_bytes(m, n, gb.GBQR_T_PANEL) + (1 << 20) + 8 * (m * n + m + n)
+
+    big_shape, long_shape, small_shape = (20000, 1000), (12000, 600), (600, 40)
+    cap = footprint(*big_shape) + footprint(*small_shape) // 2
+    assert 4 * footprint(*long_shape) <= cap and footprint(*big_shape) + footprint(*small_shape) > cap
+    ctx.serve(4, cap)
+    shapes = [long_shape] * 4 + [big_shape] + [small_shape] * 40
+    bufs, ids = [], []
+    for i, (m, n) in enumerate(shapes):
+        a, _, b = workloads.ls_problem(m, n, 1.0, 500 + i)
+        A = _gpu.device_matrix(a)
+        bd = torch.from_numpy(b).cuda()
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        bufs.append((a, b, A, bd, x))
+    torch.cuda.synchronize()
+    for i, (a, b, A, bd, x) in enumerate(bufs):
+        ids.append(ctx.submit(A, bd, x, gb.GBQR_FP64, tag=i))
+    results = [ctx.poll(r, wait=True) for r in ids]
+    ctx.stop_serving()
+    ctx.close()
+    big = results[4]
+    assert all(r.status == gb.GBQR_OK for r in results)
+    assert 0 <= big.bypassed <= 8, big.bypassed
+    assert all(r.bypassed <= 8 for r in results)
+    assert big.footprint_bytes == footprint(*big_shape)
+    a, b, _, _, x = bufs[4]
+    x_o, _ = orc.ls_solve(a, b)
+    assert np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o) <= 1e-12

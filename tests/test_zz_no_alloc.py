@@ -1,8 +1,9 @@
 """The allocation-free tall-skinny QR (gbqr_tsqr_static), for callers that
 cannot call cudaMalloc: its scratch is a fixed static device array, so it
-takes no context and no workspace.  Its output must match gbqr_factor's (the
-same TSQR base case, run with a library workspace) on two calls in a row -
-the second call finds the array holding the first call's contents."""
+takes no context and no workspace.  On two calls in a row - the second call
+finds the array holding the first call's contents - its V, T and R must match
+the oracle's element by element, and gbqr_factor's (the same TSQR base case,
+run with a library workspace) within the same tolerances."""
 
 import ctypes
 
@@ -29,16 +30,30 @@ def test_rejects_sizes_beyond_the_static_scratch():
     assert _static(gb, 4, 8, p, 4, p, 8) == gb.GBQR_EINVAL            # m < n
     assert _static(gb, 8, 4, p, 7, p, 4) == gb.GBQR_EINVAL            # lda < m
     assert _static(gb, 8, 4, p, 8, p, 3) == gb.GBQR_EINVAL            # ldt < n
-    # a tree that cannot fit 16 MiB even with the tallest leaves
+    # trees that do not fit 16 MiB: about 400,000 rows is the limit at n = 32
     assert _static(gb, 1 << 40, 32, p, 1 << 40, p, 32) == gb.GBQR_EINVAL
+    assert _static(gb, 420_000, 32, p, 420_000, p, 32) == gb.GBQR_EINVAL
     assert _static(gb, 8, 0, p, 8, p, 1) == gb.GBQR_OK                 # n = 0: nothing to do
 
 
+def _compare(a, VR, Tn, V_ref, T_ref, R_ref, label):
+    n = a.shape[1]
+    assert np.max(np.abs(np.tril(VR, -1) - np.tril(V_ref, -1))) <= _gpu.TOL_V, label
+    scale = max(1.0, float(np.max(np.abs(T_ref))))
+    assert np.max(np.abs(Tn - T_ref)) / scale <= _gpu.TOL_T, label
+    R = np.triu(VR[:n])
+    cn = np.linalg.norm(a, axis=0)
+    assert np.max(np.linalg.norm(R - R_ref, axis=0) / cn) <= _gpu.TOL_R_COL, label
+    assert np.linalg.norm(R - R_ref) / np.linalg.norm(R_ref) <= _gpu.TOL_R_NORM, label
+
+
 @pytest.mark.gpu
-@pytest.mark.parametrize("m,n,seed", [(5000, 32, 41), (1000, 17, 42), (20000, 8, 43), (33, 33 - 1, 44)])
-def test_static_scratch_matches_workspace_entry(gb, m, n, seed):
+@pytest.mark.parametrize("m,n,seed", [(5000, 32, 41), (1000, 17, 42), (20000, 8, 43), (33, 33 - 1, 44),
+                                      (250_000, 32, 45)])
+def test_static_scratch_matches_oracle_and_workspace_entry(gb, orc, m, n, seed):
     import torch
     a = workloads.gaussian(m, n, seed)
+    V_o, T_o, R_o, _ = orc.qr(a)
     stream = torch.cuda.current_stream()
     # the existing entry point: gbqr_factor with b >= n runs exactly one TSQR
     with gb.Context(0, stream) as ctx:
@@ -51,9 +66,5 @@ def test_static_scratch_matches_workspace_entry(gb, m, n, seed):
         assert st == gb.GBQR_OK, (call, st)
         torch.cuda.synchronize()
         VR, Tn = gb.to_numpy(A), gb.to_numpy(T)
-        assert np.max(np.abs(np.tril(VR, -1) - np.tril(VR_ref, -1))) <= _gpu.TOL_V, call
-        scale = max(1.0, float(np.max(np.abs(T_ref))))
-        assert np.max(np.abs(Tn - T_ref)) / scale <= _gpu.TOL_T, call
-        R, R_ref = np.triu(VR[:n]), np.triu(VR_ref[:n])
-        cn = np.linalg.norm(a, axis=0)
-        assert np.max(np.linalg.norm(R - R_ref, axis=0) / cn) <= _gpu.TOL_R_COL, call
+        _compare(a, VR, Tn, V_o, T_o, R_o, f"call {call} vs oracle")
+        _compare(a, VR, Tn, VR_ref, T_ref, np.triu(VR_ref[:n]), f"call {call} vs gbqr_factor")
