@@ -108,7 +108,7 @@ def test_bounded_bypass_of_a_large_request(gb, orc):
     def footprint(m, n):
         return gb.workspace_bytes(m, n, gb.GBQR_T_PANEL) + (1 << 20) + 8 * (m * n + m + n)
 
-    big_shape, long_shape, small_shape = (20000, 1000), (12000, 600), (600, 40)
+    big_shape, long_shape, small_shape = (30000, 1000), (4000, 256), (600, 40)
     cap = footprint(*big_shape) + footprint(*small_shape) // 2
     assert 4 * footprint(*long_shape) <= cap and footprint(*big_shape) + footprint(*small_shape) > cap
     ctx.serve(4, cap)
