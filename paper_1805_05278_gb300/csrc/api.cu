@@ -71,7 +71,7 @@ struct EventTracer final : Tracer {
     }
 };
 
-const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "trsv", "gemv", "other"};
+const char *kFamilyNames[FAM_COUNT] = {"gemm", "tc_gemm", "tsqr_up", "tsqr_down", "trsv", "gemv", "other", "batched"};
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -205,6 +205,8 @@ struct gbqr_ctx {
     std::vector<cudaEvent_t> lane_done;
     mutable std::mutex tuned_mu;           // autotuner results (gbqr_autotune*)
     std::unordered_map<uint64_t, gbqr_opts> tuned;
+    gbqr::BatchPlan *bplan[2] = {nullptr, nullptr};   // persistent batched engine: FP64, FP32 plans
+    std::vector<void *> capture_owned;    // page-locked tables a capture in progress refers to
 
     Exec exec() {
         Exec e;
@@ -243,6 +245,10 @@ bool ctx_lookup_tuned(const gbqr_ctx *cx, uint64_t key, gbqr_opts *o) {
     if (it == cx->tuned.end()) return false;
     *o = it->second;
     return true;
+}
+void ctx_free_capture_owned(gbqr_ctx *cx) {
+    for (void *h : cx->capture_owned) cudaFreeHost(h);
+    cx->capture_owned.clear();
 }
 void ctx_copy_tuned(const gbqr_ctx *from, gbqr_ctx *to) {
     std::unordered_map<uint64_t, gbqr_opts> copy;
@@ -677,6 +683,16 @@ gbqr_status apply_q_any(Work &w, bool trans, int64_t m, int64_t n, const double 
     return GBQR_OK;
 }
 
+// gbqr_factor_batched runs as one persistent kernel unless the caller asks
+// for panels wider than the cutoff, a cutoff above the persistent kernel's
+// limit or tensor-core updates: then the per-matrix panel path, spread over
+// internal streams.
+bool persistent_batch(const gbqr_opts *o) {
+    if (!o) return true;
+    const int b = o->cutoff_b ? o->cutoff_b : kBatchCutoff;
+    return b <= kMaxBatchB && (o->panel_nb == 0 || o->panel_nb == b) && o->update_prec == GBQR_FP64;
+}
+
 bool is_host_pointer(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return true; }
@@ -790,6 +806,8 @@ gbqr_status gbqr_destroy(gbqr_ctx *cx) {
     if (cx->copy) cudaStreamDestroy(cx->copy);
     for (auto st : cx->lanes) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
     for (auto ev : cx->lane_done) cudaEventDestroy(ev);
+    for (auto pl : cx->bplan) gbqr::batch_plan_free(pl);
+    gbqr::ctx_free_capture_owned(cx);
     delete cx->tracer;
     delete cx;
     return GBQR_OK;
@@ -1232,6 +1250,25 @@ gbqr_status gbqr::factor_batched_untuned(gbqr_ctx *cx, int count, const int64_t 
     if (!cx || count < 0) return GBQR_EINVAL;
     if (count == 0) return GBQR_OK;
     if (!m || !n || !A || !lda || !T || !ldt) return GBQR_EINVAL;
+    if (persistent_batch(opts)) {
+        // one persistent launch (batched.cu); T in panels of width b
+        if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+        const int b = opts && opts->cutoff_b ? opts->cutoff_b : kBatchCutoff;
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(cx->stream, &cs) != cudaSuccess) return GBQR_ECUDA;
+        const bool capturing = cs != cudaStreamCaptureStatusNone;
+        BatchPlan *pl = nullptr;
+        TRY(batched_plan<Real>(&cx->bplan[sizeof(Real) == 8 ? 0 : 1], cx->device, cx->num_sms, count, m, n, lda, ldt,
+                               b, !capturing, &pl));
+        if (capturing && cx->ws_bytes < batched_plan_bytes(pl)) return GBQR_EBUSY;
+        TRY(ensure_workspace(cx, batched_plan_bytes(pl)));
+        if (prepare_only) return GBQR_OK;
+        void *owned = nullptr;
+        const gbqr_status st = batched_enqueue<Real>(cx->exec(), pl, A, T, m, n, lda, ldt, cx->ws, cx->ws_bytes,
+                                                     &cx->dinfo->timeout, &cx->dinfo->nonfinite, capturing, &owned);
+        if (owned) cx->capture_owned.push_back(owned);
+        return st;
+    }
     int64_t mmax = 1, nmax = 1;
     std::vector<double> cost(count);
     for (int i = 0; i < count; ++i) {
@@ -1309,6 +1346,26 @@ extern "C" {
 
 size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *n, const gbqr_opts *opts) {
     if (count <= 0 || !m || !n) return 0;
+    if (persistent_batch(opts)) {
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const int b = opts && opts->cutoff_b ? opts->cutoff_b : kBatchCutoff;
+        std::vector<int64_t> ld(count), ldt(count);
+        for (int i = 0; i < count; ++i) {
+            ld[i] = std::max<int64_t>(1, m[i]);
+            ldt[i] = std::max<int64_t>(1, std::min<int64_t>(b, n[i]));
+        }
+        gbqr::BatchPlan *cache = nullptr, *pl = nullptr;
+        const gbqr_status st = gbqr::batched_plan<double>(&cache, dev, sms, count, m, n, ld.data(), ldt.data(), b,
+                                                          true, &pl);
+        const size_t bytes = st == GBQR_OK ? gbqr::batched_plan_bytes(pl) : 0;
+        gbqr::batch_plan_free(cache);
+        return bytes;
+    }
     int64_t mmax = 1, nmax = 1;
     for (int i = 0; i < count; ++i) {
         if (m[i] < n[i] || n[i] < 0) return 0;
@@ -1332,12 +1389,14 @@ size_t gbqr_batched_workspace_bytes(int count, const int64_t *m, const int64_t *
 struct gbqr_graph {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<void *> owned;   // page-locked tables its memcpy nodes read at every launch
 };
 
 gbqr_status gbqr_graph_begin(gbqr_ctx *cx) {
     if (!cx) return GBQR_EINVAL;
     if (cx->tracing) return GBQR_EBUSY;
     if (cudaSetDevice(cx->device) != cudaSuccess) return GBQR_ECUDA;
+    gbqr::ctx_free_capture_owned(cx);   // left by a capture that was not ended
     return cudaStreamBeginCapture(cx->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess ? GBQR_OK : GBQR_ECUDA;
 }
 
@@ -1350,9 +1409,11 @@ gbqr_status gbqr_graph_end(gbqr_ctx *cx, gbqr_graph **out) {
         cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) {
         cudaGetLastError();
         if (g->graph) cudaGraphDestroy(g->graph);
+        gbqr::ctx_free_capture_owned(cx);
         delete g;
         return GBQR_ECUDA;
     }
+    g->owned.swap(cx->capture_owned);
     *out = g;
     return GBQR_OK;
 }
@@ -1367,6 +1428,7 @@ gbqr_status gbqr_graph_destroy(gbqr_graph *g) {
     if (!g) return GBQR_EINVAL;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
+    for (void *h : g->owned) cudaFreeHost(h);
     delete g;
     return GBQR_OK;
 }

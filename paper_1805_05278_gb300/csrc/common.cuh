@@ -12,9 +12,10 @@ namespace gbqr {
 
 constexpr int kThreads = 256;   // threads per CTA for every kernel family
 constexpr int kMaxPanel = 64;   // largest TSQR panel width w (= cutoff b)
+constexpr int kMaxBatchB = 32;  // largest panel width of the persistent batched kernel
 
 // ---------------------------------------------------------------- tracing
-enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TRSV, FAM_GEMV, FAM_OTHER, FAM_COUNT };
+enum Family { FAM_GEMM = 0, FAM_TC_GEMM, FAM_TSQR_UP, FAM_TSQR_DOWN, FAM_TRSV, FAM_GEMV, FAM_OTHER, FAM_BATCHED, FAM_COUNT };
 
 struct Tracer {
     virtual void begin(cudaStream_t s, Family f) = 0;
@@ -138,6 +139,29 @@ template <class Real>
 gbqr_status tsqr_run(const Exec &ex, const TsqrPlan &plan, Real *A, int64_t lda,
                      Real *Tout, int64_t ldt, const TsqrWorkT<Real> &work);
 
+// ---------------------------------------------------- persistent batched QR
+// Many independent QRs in one launch (batched.cu): a plan (task list in
+// list-schedule order, workspace layout) is cached per set of shapes; each
+// call uploads the matrix table and the task list and launches one
+// persistent kernel.  T layout: panel kernels of width b (PANEL, nb = b).
+struct BatchPlan;
+void batch_plan_free(BatchPlan *pl);
+double batch_plan_estimate_ms(const BatchPlan *pl);
+size_t batched_plan_bytes(const BatchPlan *pl);
+// Validates the shapes and returns the cached plan, building it when it is
+// missing and may_build (else EBUSY).
+template <class Real>
+gbqr_status batched_plan(BatchPlan **cache, int device, int num_sms, int count, const int64_t *m,
+                         const int64_t *n, const int64_t *lda, const int64_t *ldt, int b, bool may_build,
+                         BatchPlan **out);
+// Enqueues the table upload, the counter reset and the launch on ex.stream.
+// capturing: the table is staged in page-locked memory returned in *owned,
+// which the captured graph must keep alive.
+template <class Real>
+gbqr_status batched_enqueue(const Exec &ex, BatchPlan *pl, Real *const *A, Real *const *T, const int64_t *m,
+                            const int64_t *n, const int64_t *lda, const int64_t *ldt, char *ws, size_t ws_bytes,
+                            int *timeout_flag, unsigned long long *nonfinite, bool capturing, void **owned);
+
 // ------------------------------------------------------------ small kernels
 gbqr_status fill_identity(const Exec &ex, int64_t m, int64_t n, double *Q, int64_t ldq);
 gbqr_status zero_strict_lower(const Exec &ex, int64_t n, double *T, int64_t ldt);
@@ -187,6 +211,8 @@ bool ctx_tracing(const gbqr_ctx *cx);
 void ctx_store_tuned(gbqr_ctx *cx, uint64_t key, const gbqr_opts &o);
 bool ctx_lookup_tuned(const gbqr_ctx *cx, uint64_t key, gbqr_opts *o);
 void ctx_copy_tuned(const gbqr_ctx *from, gbqr_ctx *to);
+// frees the page-locked tables recorded by a capture (after its graph is gone)
+void ctx_free_capture_owned(gbqr_ctx *cx);
 // gbqr_factor / gbqr_factor_batched without the tuner cache (the tuner's own
 // measurements must see exactly the options it passes)
 gbqr_status factor_untuned(gbqr_ctx *cx, int64_t m, int64_t n, double *A, int64_t lda, double *T, int64_t ldt,

@@ -221,13 +221,10 @@ GBQR_API gbqr_status gbqr_autotune_batched(gbqr_ctx *ctx, int count, const int64
     memset(&start, 0, sizeof start);
     start.update_prec = update_prec;
     start.cutoff_b = 16;
-    start.fanout = 0;   // the planner's adaptive fan-out
-    start.batch_streams = 128;
+    // the persistent batched kernel (panel width = cutoff b): b is its only
+    // parameter; its row-block height follows from b and shared memory
     std::vector<Axis> axes;
-    axes.push_back({&gbqr_opts::batch_streams, {16, 32, 64, 128}});
-    axes.push_back({&gbqr_opts::cutoff_b, {8, 16, 32}});
-    axes.push_back({&gbqr_opts::fanout, {0, 2, 4, 8, 16}});
-    axes.push_back({&gbqr_opts::leaf_rows, {0, 256, 512}});
+    axes.push_back({&gbqr_opts::cutoff_b, {8, 16, 24, 32}});
 
     // A batch is meant to be replayed as one captured graph (gbqr_graph_*):
     // eager calls are bound by the host enqueueing thousands of launches, so
@@ -259,18 +256,20 @@ GBQR_API gbqr_status gbqr_autotune_batched(gbqr_ctx *ctx, int count, const int64
         if (cs != GBQR_OK || ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
             cudaGetLastError();
             if (g) cudaGraphDestroy(g);
+            ctx_free_capture_owned(ctx);
             return cs != GBQR_OK ? cs : GBQR_ECUDA;
         }
         auto run = [&]() { return cudaGraphLaunch(ge, priv) == cudaSuccess ? GBQR_OK : GBQR_ECUDA; };
         if (reps == 0) {
             double probe = 0.0;
             gbqr_status s0 = time_best(priv, 1, prep, run, &probe);
-            if (s0 != GBQR_OK) { cudaGraphExecDestroy(ge); cudaGraphDestroy(g); return s0; }
+            if (s0 != GBQR_OK) { cudaGraphExecDestroy(ge); cudaGraphDestroy(g); ctx_free_capture_owned(ctx); return s0; }
             reps = reps_for(probe);
         }
         const gbqr_status s = time_best(priv, reps, prep, run, ms);
         cudaGraphExecDestroy(ge);
         cudaGraphDestroy(g);
+        ctx_free_capture_owned(ctx);   // the graph's page-locked tables
         return s;
     };
     double ms = 0.0;

@@ -97,3 +97,24 @@ def compare_factor(a, VR, T, layout, nb, orc, label="", fp32=False):
     dt = np.max(np.abs(T - T_exp)) / scale if T_exp.size else 0.0
     assert dt <= tol_t, f"{label} T differs by {dt}"
     return dv, dr_col, dt
+
+
+BATCH_B = 16   # default cutoff of gbqr_factor_batched: the persistent engine's panel width
+
+
+def q_from_panels(VR: np.ndarray, T: np.ndarray, nb: int) -> np.ndarray:
+    """Thin Q = Q_0 Q_1 ... [I; 0] from packed V\\R and the panel-layout T
+    (Q_k = I - V_k T_k V_k^T, panel k = columns k nb .. k nb + w_k - 1),
+    formed in FP64 on the host (a checker only)."""
+    VR = np.asarray(VR, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    m, n = VR.shape
+    V = oracle.unpack_v(VR)
+    Q = np.zeros((m, n))
+    Q[np.arange(n), np.arange(n)] = 1.0
+    for j0 in reversed(range(0, n, nb)):
+        w = min(nb, n - j0)
+        Vk = V[:, j0:j0 + w]
+        Tk = np.triu(T[:w, j0:j0 + w])
+        Q -= Vk @ (Tk @ (Vk.T @ Q))
+    return Q

@@ -90,8 +90,7 @@ def test_tuned_batched(gb, orc):
     shapes = workloads.batched_shapes(60, seed=5, m_range=(64, 3000), n_range=(4, 96))
     ctx = gb.Context(0)
     best, ms = ctx.autotune_batched(shapes, gb.GBQR_FP64, budget_ms=4000.0)
-    assert best.batch_streams in (16, 32, 64, 128)
-    assert best.cutoff_b in (8, 16, 32) and best.fanout in (0, 2, 4, 8, 16)
+    assert best.cutoff_b in (8, 16, 24, 32)
     assert ctx.tuned(gb.GBQR_TUNE_BATCHED) is not None
     mats = [workloads.gaussian(m, n, 500 + i) for i, (m, n) in enumerate(shapes)]
     As = [_gpu.device_matrix(a) for a in mats]
@@ -100,7 +99,7 @@ def test_tuned_batched(gb, orc):
     torch.cuda.synchronize()
     for i in (0, 7, 33, 59):
         m, n = shapes[i]
-        nb = gb.default_panel_nb(m, n)
+        nb = min(best.cutoff_b, n)            # the persistent kernel's panels: width b
         VR = gb.to_numpy(As[i])
         T = gb.to_numpy(Ts[i])[:min(nb, n), :]
         _gpu.compare_factor(mats[i], VR, T, gb.GBQR_T_PANEL, nb, orc, f"batched {i}")

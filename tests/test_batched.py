@@ -1,6 +1,10 @@
-"""Batched factorization (gbqr_factor_batched): every matrix of an uneven
-batch matches the oracle, and a captured graph of the batch reproduces the
-eager result bit for bit."""
+"""Batched factorization (gbqr_factor_batched): one persistent kernel launch
+for the whole batch (panel width b = the cutoff, T in b-wide panel blocks).
+Every matrix of an uneven batch matches the oracle - including tall ones
+whose panels span many row blocks, several panel widths, and a sample of the
+2000-matrix benchmark batch at its full sizes - the per-matrix stream path
+(wider panels) agrees with it, a NaN is reported, and a captured graph of
+the batch reproduces the eager result bit for bit."""
 
 import numpy as np
 import pytest
@@ -39,8 +43,83 @@ def test_batched_matches_oracle(gb, ctx, orc):
     st, _ = ctx.sync()
     assert st == gb.GBQR_OK
     for a, A, T in zip(mats, As, Ts):
+        nb = min(_gpu.BATCH_B, a.shape[1])
+        _gpu.compare_factor(a, gb.to_numpy(A), gb.to_numpy(T)[:nb], gb.GBQR_T_PANEL, nb, orc, f"batched {a.shape}")
+
+
+@pytest.mark.parametrize("b", [8, 16, 24, 32])
+def test_batched_panel_widths_and_tall_panels(gb, ctx, orc, b):
+    """Tall matrices (panels of several row blocks, so the flat reduction and
+    the reconstruction chain run), ragged widths, every panel width the
+    persistent kernel takes."""
+    shapes = [(20000, 40), (5003, 2 * b + 3), (b, b), (700, 1), (12345, 97), (b + 1, b), (3000, 3 * b)]
+    mats = [workloads.gaussian(m, n, 7000 + b + i) for i, (m, n) in enumerate(shapes)]
+    import torch
+    As = [_gpu.device_matrix(a) for a in mats]
+    Ts = [gb.colmajor(max(1, min(b, a.shape[1])), a.shape[1], fill=float("nan")) for a in mats]
+    ctx.factor_batched(As, Ts, gb.opts(cutoff_b=b))
+    torch.cuda.synchronize()
+    st, _ = ctx.sync()
+    assert st == gb.GBQR_OK
+    for a, A, T in zip(mats, As, Ts):
+        nb = min(b, a.shape[1])
+        _gpu.compare_factor(a, gb.to_numpy(A), gb.to_numpy(T), gb.GBQR_T_PANEL, nb, orc, f"b={b} {a.shape}")
+
+
+def test_batched_stream_path_agrees(gb, ctx, orc):
+    """panel_nb = 128 selects the per-matrix panel path (QR-EG per 128-wide
+    panel over internal streams); both engines match the oracle."""
+    shapes, mats = _batch(10, 8)
+    As, Ts = _run(gb, ctx, mats, gb.opts(panel_nb=128))
+    for a, A, T in zip(mats, As, Ts):
         nb = min(128, a.shape[1])
-        _gpu.compare_factor(a, gb.to_numpy(A), gb.to_numpy(T), gb.GBQR_T_PANEL, nb, orc, f"batched {a.shape}")
+        _gpu.compare_factor(a, gb.to_numpy(A), gb.to_numpy(T), gb.GBQR_T_PANEL, nb, orc, f"stream {a.shape}")
+
+
+def test_batched_reports_nan(gb, ctx):
+    import torch
+    shapes, mats = _batch(6, 9)
+    mats[3] = mats[3].copy()
+    mats[3][mats[3].shape[0] // 2, mats[3].shape[1] - 1] = float("nan")
+    _run(gb, ctx, mats)
+    st, info = ctx.sync()
+    assert st == gb.GBQR_ENONFINITE and info.nonfinite
+    st, _ = ctx.sync()
+    assert st == gb.GBQR_OK
+
+
+def test_batched_full_size_sample(gb, ctx):
+    """The benchmark's 2000-matrix batch (m log-uniform [256, 16384], n uniform
+    [16, 256], seeded device generator), factored in one launch exactly as the
+    bench times it; 12 matrices (the largest, the tallest, the widest and a
+    spread of others) against the all-cores oracle."""
+    import torch
+    import oracle
+    orc_all = oracle.all_cores()
+    shapes = workloads.batched_shapes(2000, workloads.BATCHED_SEED)
+    buf, offs = workloads.batched_device_buffer(shapes, workloads.BATCHED_SEED)
+    pristine = buf.clone()
+    As = [buf[o:o + m * n].view(n, m).T for (m, n), o in zip(shapes, offs)]
+    Ts = [torch.empty((n, min(128, n)), dtype=torch.float64, device="cuda").T for (m, n) in shapes]
+    ctx.factor_batched(As, Ts)
+    torch.cuda.synchronize()
+    st, _ = ctx.sync()
+    assert st == gb.GBQR_OK
+    cost = [workloads.qr_flops(m, n) for m, n in shapes]
+    pick = {int(np.argmax(cost)), int(np.argmax([m for m, _ in shapes])), int(np.argmax([n for _, n in shapes]))}
+    pick |= set(range(0, 2000, 223))
+    for i in sorted(pick):
+        m, n = shapes[i]
+        a = gb.to_numpy(pristine[offs[i]:offs[i] + m * n].view(n, m).T)
+        nb = min(_gpu.BATCH_B, n)
+        V_o, T_o, R_o, _ = orc_all.qr(a)
+        VR, T = gb.to_numpy(As[i]), gb.to_numpy(Ts[i])[:nb]
+        assert np.max(np.abs(oracle.unpack_v(VR) - V_o)) <= _gpu.TOL_V, (i, m, n)
+        R = np.triu(VR[:n])
+        assert np.linalg.norm(R - R_o) / np.linalg.norm(R_o) <= _gpu.TOL_R_NORM, (i, m, n)
+        assert np.max(np.linalg.norm(R - R_o, axis=0) / np.linalg.norm(a, axis=0)) <= _gpu.TOL_R_COL, (i, m, n)
+        Tb = _gpu.panel_blocks_of(T_o, nb)
+        assert np.max(np.abs(T - Tb)) / max(1.0, np.max(np.abs(Tb))) <= _gpu.TOL_T, (i, m, n)
 
 
 def test_batched_mixed_precision_runs(gb, ctx, orc):

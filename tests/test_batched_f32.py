@@ -42,9 +42,9 @@ def test_f32_batched_matches_oracle(gb, orc):
     st, _ = ctx.sync()
     assert st == gb.GBQR_OK
     for a, A, T in zip(mats, As, Ts):
-        nb = min(128, a.shape[1])
+        nb = min(_gpu.BATCH_B, a.shape[1])
         VR = A.cpu().numpy().astype(np.float64)
-        Tn = T.cpu().numpy().astype(np.float64)
+        Tn = T.cpu().numpy().astype(np.float64)[:nb]
         _gpu.compare_factor(a.astype(np.float64), VR, Tn, gb.GBQR_T_PANEL, nb, orc, f"fp32 {a.shape}", fp32=True)
     ctx.close()
 
@@ -58,10 +58,8 @@ def test_f32_orthogonality_and_backward_error(gb, orc):
     As, Ts = _run32(gb, ctx, [a])
     VR = As[0].cpu().numpy().astype(np.float64)
     m, n = a.shape
-    v = np.tril(VR, -1)
-    v[np.arange(n), np.arange(n)] = 1.0
-    T = Ts[0].cpu().numpy().astype(np.float64)                  # one 96-wide panel: T is 96 x 96
-    q = np.eye(m)[:, :n] - v @ (T @ v[:n, :].T)                 # Q [I; 0] = [I; 0] - V T V1^T
+    T = Ts[0].cpu().numpy().astype(np.float64)                  # 16-wide panel blocks
+    q = _gpu.q_from_panels(VR, T, _gpu.BATCH_B)
     r = np.triu(VR[:n])
     assert np.linalg.norm(q.T @ q - np.eye(n), 2) <= _gpu.TOL32_BACKWARD
     assert np.linalg.norm(a - q @ r) / np.linalg.norm(a) <= _gpu.TOL32_BACKWARD

@@ -41,7 +41,7 @@ def test_batch_with_degenerate_shapes(gb, orc, dtype):
         if n == 0:
             continue
         a_in = a.astype(np.float32).astype(np.float64) if dtype == "f32" else a
-        nb = min(128, n)
+        nb = min(_gpu.BATCH_B, n)
         _gpu.compare_factor(a_in, A.cpu().numpy(), T.cpu().numpy()[:nb], gb.GBQR_T_PANEL, nb, orc,
                             f"{dtype} {m}x{n}", fp32=(dtype == "f32"))
     ctx.close()
