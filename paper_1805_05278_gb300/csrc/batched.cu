@@ -284,12 +284,15 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
     build_t(Ui, X, rU, Cm, w);                 // U^{-1}: strict upper of X, diagonal 1 / rU
     unit_lower_inverse(X, Li, Cm, w);          // L^{-1}
     {
-        // T = U S L^{-T}
+        // T = U S L^{-T}; a last panel narrower than b gets zeros in rows
+        // w .. nb-1 of its block (nb = min(b, n) rows: the panel layout)
         Real *Tout = M.T + (int64_t)j0 * M.ldt;
-        for (int idx = tid; idx < ww; idx += nthr) {
-            const int i = idx % w, c = idx / w;
+        const int nbr = min(b, M.n);
+        for (int idx = tid; idx < nbr * w; idx += nthr) {
+            const int i = idx % nbr, c = idx / nbr;
             Real t = Real(0);
-            for (int l = i; l <= c; ++l) t = rfma(X[i + l * w] * Sg[l], (l == c) ? Real(1) : Li[c + l * w], t);
+            if (i < w)
+                for (int l = i; l <= c; ++l) t = rfma(X[i + l * w] * Sg[l], (l == c) ? Real(1) : Li[c + l * w], t);
             Tout[i + (int64_t)c * M.ldt] = t;
         }
     }

@@ -151,6 +151,7 @@ def test_graph_capture_reproduces_eager(gb):
         graph.launch()
         torch.cuda.synchronize()
         for A, T, EA, ET in zip(As, Ts, eager_A, eager_T):
-            assert torch.equal(A, EA) and torch.equal(T, ET)
+            nb = min(_gpu.BATCH_B, T.shape[1])        # rows of the b-wide panel layout
+            assert torch.equal(A, EA) and torch.equal(T[:nb], ET[:nb])
     graph.close()
     ctx.close()
