@@ -247,10 +247,11 @@ def _time_batch_graph(gb, ctx, stream, buf, pristine, As, Ts, o, steps):
 
 def measure_batched(gb, dev, args):
     """The batched tall-skinny workload: args.batched matrices, m log-uniform
-    in [256, 16384], n uniform in [16, 256], factored by one captured graph
-    launch of gbqr_factor_batched (FP64), then the same matrices rounded to
-    FP32 by gbqr_factor_batched_f32.  Each timed step restores the inputs with
-    one device copy, then launches the graph."""
+    in [256, 16384], n uniform in [16, 256], factored by gbqr_factor_batched
+    (FP64: one persistent kernel launch for the whole batch, captured in a
+    graph with its table upload), then the same matrices rounded to FP32 by
+    gbqr_factor_batched_f32.  Each timed step restores the inputs with one
+    device copy (untimed), then launches the graph."""
     import torch
     shapes = workloads.batched_shapes(args.batched, workloads.BATCHED_SEED)
     buf, offs = workloads.batched_device_buffer(shapes, workloads.BATCHED_SEED, f"cuda:{dev}")
@@ -271,8 +272,10 @@ def measure_batched(gb, dev, args):
     out = {"workload": f"{len(shapes)} matrices, m log-uniform [256, 16384], n uniform [16, 256], "
                        f"iid N(0,1), seed {workloads.BATCHED_SEED}",
            "total_flops": flops, "ms_per_batch": ms, "tflops": flops / (ms * 1e-3) / 1e12,
+           "frac_of_fp64_peak": flops / (ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
            "matrices_per_s": len(shapes) / (ms * 1e-3), "graph_launches_per_batch": 1, "status": int(st),
-           "streams": o.batch_streams or 128, "cutoff_b": o.cutoff_b or 16,
+           "engine": "one persistent kernel launch (panel and update tasks, list-scheduled), captured in a graph",
+           "kernel_launches_per_batch": 1, "cutoff_b": o.cutoff_b or 16,
            "tuned": tuned, "tuned_ms": tune_ms, "dtype": "f64"}
     del As, Ts, buf, pristine
     # FP32: the same matrices rounded to float32, FP32 arithmetic throughout
@@ -286,7 +289,7 @@ def measure_batched(gb, dev, args):
     st32, _ = ctx.sync()
     out["fp32"] = {"ms_per_batch": ms32, "tflops": flops / (ms32 * 1e-3) / 1e12,
                    "matrices_per_s": len(shapes) / (ms32 * 1e-3), "status": int(st32), "dtype": "f32",
-                   "cutoff_b": args.batched_cutoff32 or 16, "streams": args.batched_streams or 128}
+                   "cutoff_b": args.batched_cutoff32 or 16, "kernel_launches_per_batch": 1}
     ctx.close()
     return out
 

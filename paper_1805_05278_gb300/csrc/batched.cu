@@ -44,10 +44,8 @@
 namespace gbqr {
 namespace {
 
-constexpr int kUpdRows = 64;    // rows per chunk of an update task
 constexpr int kUpdCols = 64;    // columns of an update task (the look-ahead block excepted)
 
-constexpr int kEntBatch = 8;    // C entries a thread loads ahead in the update's second pass
 constexpr size_t kSmemBudget = 110 * 1024;   // two CTAs per SM
 
 template <class Real>
@@ -65,7 +63,7 @@ struct BParams {
     const BMat<Real> *mats;
     const int4 *tasks;      // (matrix, k, c0, c1): a panel task when c0 == c1 (== k)
     int ntasks;
-    int b, hblk, ldS;
+    int b, hblk, ldS, hup;    // panel width, panel row-block height, its shared ld, update chunk rows
     int *state;             // per (matrix, column block): panels applied, +1 once factored
     unsigned *next;         // task dispenser
     int *abort;             // raised by a wait that ran out; every CTA then stops
@@ -132,6 +130,31 @@ __device__ bool wait_deps(const BParams<Real> &p, const int *st, int k, int c0, 
     return true;
 }
 
+// Asynchronous global -> shared copies (cp.async, one element each: the
+// column segments of a chunk need not be 16-byte aligned).  The waits on a
+// task's counters end with an acquire at GPU scope, which orders these
+// copies after the writes that other CTAs released.
+template <class Real>
+__device__ __forceinline__ void cp_async(Real *dst_smem, const Real *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    if constexpr (sizeof(Real) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// dst(r, c) = src(r, c) for an h x w block, the whole CTA, asynchronously.
+template <class Real>
+__device__ __forceinline__ void async_block(Real *dst, int ldd, const Real *src, int64_t lds, int h, int w) {
+    for (int idx = threadIdx.x; idx < h * w; idx += blockDim.x) {
+        const int c = idx / h, r = idx - c * h;
+        cp_async(dst + r + c * ldd, src + r + (int64_t)c * lds);
+    }
+}
+
 // M <- T (V1^T B) for w <= kMaxBatchB (the leaf_z of the TSQR downsweep with
 // fewer registers): V1 unit lower (column-major, ld w, strict lower part
 // read), T upper in M on entry, B upper; C is w x w scratch.
@@ -169,11 +192,34 @@ __device__ void leaf_z_small(const Real *V1, const Real *B, Real *C, Real *M, in
     __syncthreads();
 }
 
+// V rows of one row block: out(r, c) = -sum_{i <= c} Y(r, i) Z(i, c) for
+// rows r0 .. r0 + h - 1 of S (ld ldS) and Z upper w x w (ld w), written to
+// the panel at out (ld lda).  Each thread takes whole rows with Y(r, :) in
+// registers, so the w column sums are independent chains.
+template <int MaxB, class Real>
+__device__ __forceinline__ void v_rows(const Real *S, int ldS, int r0, int h, const Real *Z, int w, Real *out,
+                                       int64_t lda) {
+    for (int r = r0 + (int)threadIdx.x; r < r0 + h; r += blockDim.x) {
+        Real y[MaxB];
+#pragma unroll
+        for (int i = 0; i < MaxB; ++i) y[i] = (i < w) ? S[r + (size_t)i * ldS] : Real(0);
+#pragma unroll
+        for (int c = 0; c < MaxB; ++c) {
+            if (c < w) {
+                Real s = Real(0);
+#pragma unroll
+                for (int i = 0; i <= c; ++i) s = rfma(y[i], Z[i + c * w], s);
+                out[r + (int64_t)c * lda] = -s;
+            }
+        }
+    }
+}
+
 // Panel task (flat-tree TSQR in one CTA, then the Householder
 // reconstruction); returns non-zero if the panel held a NaN or Inf.
 // Shared memory: S (ldS x b), then Tt, G, Mx, Bm, Cm, X, Li, Ui (b x b each,
 // used with leading dimension w), then 7 b reflector scalars and signs.
-template <class Real>
+template <int MaxB, class Real>
 __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Real *sm, Real *tscr) {
     const int b = p.b, tid = threadIdx.x, nthr = blockDim.x;
     const int j0 = k * b;
@@ -195,7 +241,9 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
 
     // ---- upsweep: block 0 as a leaf, then each block stacked under R
     const int h0 = rb(1);
-    load_block(S, ldS, A, lda, h0, w);
+    async_block(S, ldS, A, lda, h0, w);
+    cp_commit();
+    cp_wait<0>();
     __syncthreads();
     bad |= scan_block(S, ldS, h0, w);
     householder_block(S, ldS, w, LeafRows{h0}, rf, G);
@@ -214,7 +262,9 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
     __syncthreads();
     for (int q = 1; q < P; ++q) {
         const int r0 = rb(q), hq = rb(q + 1) - r0;
-        load_block(S + w, ldS, A + r0, lda, hq, w);
+        async_block(S + w, ldS, A + r0, lda, hq, w);
+        cp_commit();
+        cp_wait<0>();
         __syncthreads();
         bad |= scan_block(S + w, ldS, hq, w);
         householder_block(S, ldS, w, StackRows{w, hq}, rf, G);
@@ -308,16 +358,12 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
     for (int q = P - 1; q >= 1; --q) {
         const int r0 = rb(q), hq = rb(q + 1) - r0;
         for (int idx = tid; idx < ww; idx += nthr) Mx[idx] = tscr[(size_t)q * bb + idx];
-        load_block(S, ldS, A + r0, lda, hq, w);
-        __syncthreads();
+        async_block(S, ldS, A + r0, lda, hq, w);
+        cp_commit();
         upper_upper(Mx, Bm, Cm, w, Real(1));
+        cp_wait<0>();
         __syncthreads();
-        for (int idx = tid; idx < hq * w; idx += nthr) {
-            const int r = idx % hq, c = idx / hq;
-            Real s = Real(0);
-            for (int i = 0; i <= c; ++i) s = rfma(S[r + (size_t)i * ldS], Cm[i + c * w], s);
-            A[r0 + r + (int64_t)c * lda] = -s;
-        }
+        v_rows<MaxB>(S, ldS, 0, hq, Cm, w, A + r0, lda);
         for (int idx = tid; idx < ww; idx += nthr) Bm[idx] -= Cm[idx];
         __syncthreads();
     }
@@ -327,16 +373,12 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
         Li[idx] = (i > c) ? __ldcg(A + i + (int64_t)c * lda) : Real(0);
         Mx[idx] = tscr[idx];
     }
-    load_block(S, ldS, A, lda, h0, w);
+    async_block(S, ldS, A, lda, h0, w);
+    cp_commit();
+    cp_wait<0>();
     __syncthreads();
     leaf_z_small(Li, Bm, Cm, Mx, w);
-    const int hb = h0 - w;
-    for (int idx = tid; idx < hb * w; idx += nthr) {
-        const int r = w + idx % hb, c = idx / hb;
-        Real s = Real(0);
-        for (int i = 0; i <= c; ++i) s = rfma(S[r + (size_t)i * ldS], Mx[i + c * w], s);
-        A[r + (int64_t)c * lda] = -s;
-    }
+    v_rows<MaxB>(S, ldS, w, h0 - w, Mx, w, A, lda);
     // top rows: L strictly below the diagonal, R = -S R_tree on and above
     for (int idx = tid; idx < ww; idx += nthr) {
         const int i = idx % w, c = idx / w;
@@ -347,9 +389,10 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
 
 // Update task: C <- (I - V T V^T)^T C for columns [c0 b, min(c1 b, n)) and
 // rows k b .. m-1, V = panel k's reflectors (unit lower; R above them is
-// masked), T = its kernel.  Two passes over the rows in chunks of kUpdRows:
-// W = V^T C (each thread accumulates its W entries over every row), then
-// W = T^T W, then C -= V W.
+// masked), T = its kernel.  Two passes over the rows in chunks of H rows,
+// each chunk copied asynchronously into one of two stages while the other
+// stage is computed on: W = V^T C (each thread accumulates its W entries
+// over every row), then W = T^T W, then C -= V W.
 template <int MaxB, class Real>
 __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, int c0, int c1, Real *sm) {
     constexpr int kMaxOut = (MaxB * kUpdCols + kThreads - 1) / kThreads;   // W entries per thread
@@ -360,11 +403,28 @@ __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, 
     const Real *V = M.A + j0 + (int64_t)j0 * lda;
     Real *C = M.A + j0 + (int64_t)col0 * lda;
     const Real *Tg = M.T + (int64_t)j0 * M.ldt;
-    constexpr int H = kUpdRows, ldc = kUpdRows + 1;   // odd stride: no bank conflicts across j
-    Real *Vs = sm;                     // H x w
-    Real *Cs = Vs + ldc * b;           // H x cw
-    Real *Ws = Cs + ldc * kUpdCols;    // w x cw, ld b
+    const int H = p.hup, ldc = p.hup + 1;             // odd stride: no bank conflicts across j
+    const int vst = ldc * b, cst = ldc * kUpdCols;    // stage sizes
+    Real *Vs = sm;                     // 2 stages of H x w
+    Real *Cs = Vs + 2 * vst;           // 2 stages of H x cw
+    Real *Ws = Cs + 2 * cst;           // w x cw, ld b
     Real *Ts = Ws + b * kUpdCols;      // w x w, ld b
+    const int nch = (mr + H - 1) / H;
+    auto issue = [&](int ch, bool with_c) {
+        const int r0 = ch * H, hc = min(H, mr - r0), st = ch & 1;
+        async_block(Vs + st * vst, ldc, V + r0, lda, hc, w);
+        if (with_c) async_block(Cs + st * cst, ldc, C + r0, lda, hc, cw);
+        cp_commit();
+    };
+    // V's top: 1 on the diagonal, 0 above it (R lives there); H >= b, so
+    // only chunk 0 holds those rows
+    auto mask_top = [&](Real *Vc, int hc) {
+        for (int idx = tid; idx < min(hc, w) * w; idx += nthr) {
+            const int r = idx % w, j = idx / w;
+            if (r <= j) Vc[r + j * ldc] = (r == j) ? Real(1) : Real(0);
+        }
+    };
+    issue(0, true);
     for (int idx = tid; idx < w * w; idx += nthr) {
         const int i = idx % w, j = idx / w;
         Ts[i + j * b] = (i <= j) ? __ldcg(Tg + i + (int64_t)j * M.ldt) : Real(0);
@@ -373,32 +433,27 @@ __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, 
     Real acc[kMaxOut];
 #pragma unroll
     for (int q = 0; q < kMaxOut; ++q) acc[q] = Real(0);
-    for (int r0 = 0; r0 < mr; r0 += H) {
-        const int hc = min(H, mr - r0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) { issue(ch + 1, true); cp_wait<1>(); }
+        else cp_wait<0>();
         __syncthreads();
-        load_block(Vs, ldc, V + r0, lda, hc, w);
-        load_block(Cs, ldc, C + r0, lda, hc, cw);
-        __syncthreads();
-        if (r0 < w) {   // V's top: 1 on the diagonal, 0 above it (R lives there)
-            for (int idx = tid; idx < hc * w; idx += nthr) {
-                const int r = idx % hc, j = idx / hc, rg = r0 + r;
-                if (rg <= j) Vs[r + j * ldc] = (rg == j) ? Real(1) : Real(0);
-            }
-            __syncthreads();
-        }
+        const int hc = min(H, mr - ch * H), st = ch & 1;
+        Real *Vc = Vs + st * vst, *Cc = Cs + st * cst;
+        if (ch == 0) { mask_top(Vc, hc); __syncthreads(); }
 #pragma unroll
         for (int q = 0; q < kMaxOut; ++q) {
             const int o = tid + q * kThreads;
             if (o < nout) {
                 const int j = o % w, c = o / w;
-                const Real *vp = Vs + j * ldc, *cp = Cs + c * ldc;
+                const Real *vp = Vc + j * ldc, *cp = Cc + c * ldc;
                 Real a = acc[q];
                 for (int r = 0; r < hc; ++r) a = rfma(vp[r], cp[r], a);
                 acc[q] = a;
             }
         }
+        __syncthreads();                 // the stage is reloaded two chunks on
     }
-    __syncthreads();
+    issue(0, true);                      // pass 2's first chunk, under the T^T W product
 #pragma unroll
     for (int q = 0; q < kMaxOut; ++q) {
         const int o = tid + q * kThreads;
@@ -421,37 +476,20 @@ __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, 
         const int o = tid + q * kThreads;
         if (o < nout) Ws[o % w + (o / w) * b] = acc[q];
     }
-    for (int r0 = 0; r0 < mr; r0 += H) {
-        const int hc = min(H, mr - r0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) { issue(ch + 1, true); cp_wait<1>(); }
+        else cp_wait<0>();
         __syncthreads();
-        load_block(Vs, ldc, V + r0, lda, hc, w);
+        const int r0 = ch * H, hc = min(H, mr - r0), st = ch & 1;
+        Real *Vc = Vs + st * vst, *Cc = Cs + st * cst;
+        if (ch == 0) { mask_top(Vc, hc); __syncthreads(); }
+        for (int e = tid; e < hc * cw; e += nthr) {
+            const int c = e / hc, r = e - c * hc;
+            Real s = Real(0);
+            for (int j = 0; j < w; ++j) s = rfma(Vc[r + j * ldc], Ws[j + c * b], s);
+            C[r0 + r + (int64_t)c * lda] = Cc[r + c * ldc] - s;
+        }
         __syncthreads();
-        if (r0 < w) {
-            for (int idx = tid; idx < hc * w; idx += nthr) {
-                const int r = idx % hc, j = idx / hc, rg = r0 + r;
-                if (rg <= j) Vs[r + j * ldc] = (rg == j) ? Real(1) : Real(0);
-            }
-            __syncthreads();
-        }
-        const int nent = hc * cw;
-        for (int e0 = 0; e0 < nent; e0 += kEntBatch * kThreads) {
-            Real x[kEntBatch];
-#pragma unroll
-            for (int q = 0; q < kEntBatch; ++q) {
-                const int e = e0 + tid + q * kThreads;
-                if (e < nent) x[q] = __ldcg(C + r0 + e % hc + (int64_t)(e / hc) * lda);
-            }
-#pragma unroll
-            for (int q = 0; q < kEntBatch; ++q) {
-                const int e = e0 + tid + q * kThreads;
-                if (e < nent) {
-                    const int r = e % hc, c = e / hc;
-                    Real s = Real(0);
-                    for (int j = 0; j < w; ++j) s = rfma(Vs[r + j * ldc], Ws[j + c * b], s);
-                    C[r0 + r + (int64_t)c * lda] = x[q] - s;
-                }
-            }
-        }
     }
 }
 
@@ -481,7 +519,7 @@ __global__ void __launch_bounds__(kThreads, 2) batched_qr_kernel(BParams<Real> p
         const int mi = s_task[0], k = s_task[1], c0 = s_task[2], c1 = s_task[3];
         const BMat<Real> M = p.mats[mi];
         int bad = 0;
-        if (c0 == c1) bad = panel_task(p, M, k, sm, tscr);
+        if (c0 == c1) bad = panel_task<MaxB>(p, M, k, sm, tscr);
         else update_task<MaxB>(p, M, k, c0, c1, sm);
         bad = __syncthreads_or(bad);
         if (threadIdx.x == 0) {
@@ -504,8 +542,16 @@ const void *kernel_for(int b) {
 size_t panel_smem(int b, int hblk, size_t real) {
     return real * ((size_t)(hblk + b) * b + 8 * (size_t)b * b + 7 * (size_t)b);
 }
-size_t update_smem(int b, size_t real) {
-    return real * ((size_t)(kUpdRows + 1) * (b + kUpdCols) + (size_t)b * kUpdCols + (size_t)b * b);
+size_t update_smem(int b, int hup, size_t real) {
+    return real * (2 * (size_t)(hup + 1) * (b + kUpdCols) + (size_t)b * kUpdCols + (size_t)b * b);
+}
+
+// Rows per update chunk: the most (a multiple of 16, at most 128) whose two
+// stages fit the shared-memory budget.
+int update_rows(int b, size_t real) {
+    int h = 128;
+    while (h > 16 && update_smem(b, h, real) > kSmemBudget) h -= 16;
+    return h;
 }
 
 // Tallest row block a panel task's shared memory holds (a multiple of 32).
@@ -527,7 +573,7 @@ uint64_t fnv(uint64_t h, const void *p, size_t n) {
 struct BatchPlan {
     uint64_t key = 0;            // shapes, leading dimensions, b, scalar size, device
     size_t real = 8;
-    int b = 16, hblk = 0, ldS = 0, grid = 0, ntasks = 0, nstate = 0, tscr_blocks = 0, count = 0;
+    int b = 16, hblk = 0, hup = 64, ldS = 0, grid = 0, ntasks = 0, nstate = 0, tscr_blocks = 0, count = 0;
     size_t smem = 0;
     size_t off_tasks = 0, off_state = 0, off_tscr = 0, total = 0, table_bytes = 0, state_bytes = 0;
     size_t tscr_stride = 0;
@@ -682,7 +728,8 @@ gbqr_status batched_plan(BatchPlan **cache, int device, int num_sms, int count, 
     BatchPlan *pl = *cache;
     if (pl && pl->key == key) { *out = pl; return GBQR_OK; }
     if (!may_build) return GBQR_EBUSY;
-    const size_t smem = std::max(panel_smem(b, hblk, sizeof(Real)), update_smem(b, sizeof(Real)));
+    const int hup = update_rows(b, sizeof(Real));
+    const size_t smem = std::max(panel_smem(b, hblk, sizeof(Real)), update_smem(b, hup, sizeof(Real)));
     const void *kern = kernel_for<Real>(b);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return GBQR_ECUDA;
@@ -698,6 +745,7 @@ gbqr_status batched_plan(BatchPlan **cache, int device, int num_sms, int count, 
     pl->real = sizeof(Real);
     pl->b = b;
     pl->hblk = hblk;
+    pl->hup = hup;
     pl->ldS = hblk + b;
     pl->smem = smem;
     pl->grid = per_sm * num_sms;
@@ -745,6 +793,7 @@ gbqr_status batched_enqueue(const Exec &ex, BatchPlan *pl, Real *const *A, Real 
     p.ntasks = pl->ntasks;
     p.b = pl->b;
     p.hblk = pl->hblk;
+    p.hup = pl->hup;
     p.ldS = pl->ldS;
     p.state = reinterpret_cast<int *>(ws + pl->off_state);
     p.next = reinterpret_cast<unsigned *>(p.state + pl->nstate);
