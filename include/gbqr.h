@@ -497,6 +497,14 @@ GBQR_API gbqr_status gbqr_fp64_peak(int device, int kind, int iters, double *tfl
  * Errors: EINVAL, ENOMEM, ECUDA. */
 GBQR_API gbqr_status gbqr_selftest_wait_timeout(int device, int *completed);
 
+/* Failure-detection self-test of the persistent batched kernel: one CTA is
+ * given a task whose dependency never completes, so its bounded wait (wait_ms,
+ * 1..10000) must run out, raise the kernel's abort and timeout flags and
+ * return.  Expected: GBQR_ETIMEOUT with *completed = 0, and the device still
+ * usable.  The paper has no counterpart.  Synchronous; allocates 1 KB.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+GBQR_API gbqr_status gbqr_selftest_batched_wait(int device, int wait_ms, int *completed);
+
 /* Human-readable name of a status. */
 GBQR_API const char *gbqr_strerror(gbqr_status s);
 

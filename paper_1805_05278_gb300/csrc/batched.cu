@@ -822,3 +822,58 @@ template gbqr_status batched_enqueue<float>(const Exec &, BatchPlan *, float *co
                                             char *, size_t, int *, unsigned long long *, bool, void **);
 
 }  // namespace gbqr
+
+// Failure-detection self-test of the dependency wait: one CTA of the FP64
+// kernel gets a task list holding only update(0, 0, 1, 2), whose panel
+// (block 0 factored) never runs, so its wait must give up after wait_ms,
+// raise the abort and timeout flags and return.  completed: block 1's
+// counter afterwards (0: the update did not run).
+extern "C" GBQR_API gbqr_status gbqr_selftest_batched_wait(int device, int wait_ms, int *completed) {
+    using namespace gbqr;
+    if (!completed || wait_ms < 1 || wait_ms > 10000) return GBQR_EINVAL;
+    *completed = -1;
+    if (cudaSetDevice(device) != cudaSuccess) return GBQR_ECUDA;
+    // [mats | tasks | state (2) + dispenser + abort | timeout flag] in one allocation
+    const size_t off_tasks = 256, off_state = 512, off_flag = 768, bytes = 1024;
+    char *d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return GBQR_ENOMEM; }
+    gbqr_status st = GBQR_OK;
+    BMat<double> bm;
+    bm.A = reinterpret_cast<double *>(d); bm.T = reinterpret_cast<double *>(d);   // never dereferenced
+    bm.lda = 64; bm.ldt = 16; bm.m = 64; bm.n = 32; bm.state0 = 0; bm.pad = 0;
+    const int4 task = make_int4(0, 0, 1, 2);
+    if (cudaMemset(d, 0, bytes) != cudaSuccess || cudaMemcpy(d, &bm, sizeof bm, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d + off_tasks, &task, sizeof task, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = GBQR_ECUDA;
+    const size_t smem = std::max(panel_smem(16, 64, 8), update_smem(16, 16, 8));
+    if (st == GBQR_OK &&
+        cudaFuncSetAttribute(batched_qr_kernel<16, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+        st = GBQR_ECUDA;
+    int h[2] = {0, 0};
+    if (st == GBQR_OK) {
+        BParams<double> p;
+        p.mats = reinterpret_cast<const BMat<double> *>(d);
+        p.tasks = reinterpret_cast<const int4 *>(d + off_tasks);
+        p.ntasks = 1;
+        p.b = 16; p.hblk = 64; p.ldS = 80; p.hup = 16;
+        p.state = reinterpret_cast<int *>(d + off_state);
+        p.next = reinterpret_cast<unsigned *>(p.state + 2);
+        p.abort = p.state + 3;
+        p.timeout = reinterpret_cast<int *>(d + off_flag);
+        p.nonfinite = reinterpret_cast<unsigned long long *>(d + off_flag + 8);
+        p.tscr = reinterpret_cast<double *>(d);
+        p.tscr_stride = 0;
+        p.tscr_blocks = 0;
+        p.wait_ns = (long long)wait_ms * 1000000ll;
+        batched_qr_kernel<16, double><<<1, kThreads, smem>>>(p);
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(&h[0], d + off_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(&h[1], d + off_state + sizeof(int), sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = GBQR_ECUDA;
+    }
+    cudaFree(d);
+    if (st != GBQR_OK) return st;
+    *completed = h[1];
+    return h[0] ? GBQR_ETIMEOUT : GBQR_OK;
+}

@@ -2,7 +2,8 @@
 tensor-core GEMM uses gives up after its time limit on a barrier nothing
 arrives at, raises the error flag and returns; the host reads GBQR_ETIMEOUT
 and the device keeps working (a mixed-precision factorization right after
-matches the oracle)."""
+matches the oracle).  The same for the persistent batched kernel's bounded
+dependency wait, on a task whose dependency never completes."""
 
 import ctypes
 
@@ -29,4 +30,22 @@ def test_bounded_wait_times_out_and_device_survives(gb, orc):
     R = np.triu(VR[:300])
     _, _, R_o, _ = orc.qr(a)
     assert np.linalg.norm(R - R_o) / np.linalg.norm(R_o) <= 50 * np.linalg.cond(a) * 2.0 ** -22
+    ctx.close()
+
+
+def test_batched_dependency_wait_times_out_and_device_survives(gb, orc):
+    import torch
+    completed = ctypes.c_int(-2)
+    st = gb.gbqr_selftest_batched_wait(0, 300, ctypes.byref(completed))
+    assert st == gb.GBQR_ETIMEOUT and completed.value == 0
+    ctx = gb.Context(0)
+    mats = [workloads.gaussian(m, n, 40 + i) for i, (m, n) in enumerate([(900, 70), (3000, 33), (64, 64)])]
+    As = [_gpu.device_matrix(a) for a in mats]
+    Ts = [gb.colmajor(16, a.shape[1], fill=float("nan")) for a in mats]
+    ctx.factor_batched(As, Ts)
+    torch.cuda.synchronize()
+    st, _ = ctx.sync()
+    assert st == gb.GBQR_OK
+    for a, A, T in zip(mats, As, Ts):
+        _gpu.compare_factor(a, gb.to_numpy(A), gb.to_numpy(T), gb.GBQR_T_PANEL, 16, orc, f"after timeout {a.shape}")
     ctx.close()

@@ -139,8 +139,10 @@ def qr_flops_partial(m: int, n: int, k: int) -> float:
 SMALL_1024x128 = Workload("gaussian_1024x128", 1024, 128, seed=0, graded=False, rhs_seed=1)
 TALL_32768x2048 = Workload("graded_32768x2048", 32768, 2048, seed=2, graded=True)
 SQUARE_8192 = Workload("graded_8192x8192", 8192, 8192, seed=3, graded=True)
+# A quarter-size square case for profiling captures (134 MB: still larger than L2).
+SQUARE_4096 = Workload("graded_4096x4096", 4096, 4096, seed=4, graded=True)
 
-WORKLOADS = {w.name: w for w in (SMALL_1024x128, TALL_32768x2048, SQUARE_8192)}
+WORKLOADS = {w.name: w for w in (SMALL_1024x128, TALL_32768x2048, SQUARE_8192, SQUARE_4096)}
 
 
 def log_uniform_int(rng: np.random.Generator, lo: int, hi: int) -> int:
