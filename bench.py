@@ -53,11 +53,17 @@ SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0
 FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + write) of dgemm launches over their algorithmic bytes
-# 8 (MK + KN + 2MN), from an ncu capture of a few launches of this
-# configuration; the roofline's traffic is null for any other configuration.
+# 8 (MK + KN + 2MN), from an ncu capture of every dgemm launch of the
+# quarter-size graded 4096 x 4096 factorization with the same panel width,
+# cutoff and engine (one-pass metrics); the roofline's traffic is that ratio
+# times the measured pass's algorithmic bytes per launch, null for any other
+# configuration.
 DGEMM_TRAFFIC_RATIO = {
     # (workload, panel_nb, cutoff_b, engine): ratio
+    ("graded_8192x8192", 128, 16, "dfma"): 0.764,
+    ("graded_4096x4096", 128, 16, "dfma"): 0.764,
 }
+DGEMM_TRAFFIC_SOURCE = "ncu: all dgemm launches of graded 4096x4096 (nb 128, b 16, DFMA), dram read+write / algorithmic"
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs peak; LS solves/s, p99 ms: mixed vs FP64"
 
 
@@ -735,6 +741,7 @@ def run_gbqr(args):
         "traffic_unit": "bytes per launch (dram read + write): ncu ratio to algorithmic bytes x this pass's "
                         "algorithmic bytes per launch",
         "traffic_ratio_ncu": ratio,
+        "traffic_source": DGEMM_TRAFFIC_SOURCE if ratio else None,
         "algorithmic_bytes_per_launch": alg_bytes,
         "launches": gemm.get("launches"), "share_of_step": share,
         "serial_ms_per_step": serial_ms / max(1, args.roofline_steps),
