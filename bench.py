@@ -100,6 +100,7 @@ def parse():
     p.add_argument("--ls-solves", type=int, default=3, help="timed least-squares solves per grid point and precision (0: skip)")
     p.add_argument("--ls-decades", default="2,6,10", help="column-grading decades (kappa ~ 10^d x kappa(Gaussian))")
     p.add_argument("--ls-shapes", default="32768x2048,8192x8192")
+    p.add_argument("--ls-precisions", default="fp64,mixed", help="which LS paths to time (fp64, mixed)")
     p.add_argument("--ls-oracle-shapes", default="32768x2048",
                    help="LS shapes whose results are also compared with the CPU oracle's solution")
     p.add_argument("--no-ls-kappa", action="store_true", help="skip the condition estimate (torch.linalg)")
@@ -353,6 +354,8 @@ def measure_ls(gb, ctx, dev, args):
             row = {"m": m, "n": n, "decades": d, "kappa_est": kappa, "seed": seed}
             xs = {}
             for prec, name in [(gb.GBQR_FP64, "fp64"), (gb.GBQR_MIXED_SPLITBF16, "mixed_splitbf16")]:
+                if name.split("_")[0] not in args.ls_precisions.split(","):
+                    continue
                 # the tuner's choice for this shape class and precision (cached in ctx,
                 # picked up by gbqr_ls_solve); once per shape
                 if args.ls_autotune_ms > 0 and ctx.tuned(gb.GBQR_TUNE_FACTOR, m, n, gb.GBQR_T_PANEL, prec) is None:
@@ -379,6 +382,11 @@ def measure_ls(gb, ctx, dev, args):
                              "gmres_steps": int(info.gmres_steps), "lib_backward_err": float(info.backward_err),
                              "rel_err_vs_xtrue": float(torch.linalg.norm(x - xt) / torch.linalg.norm(xt)),
                              "backward_err": bwd}
+            if len(xs) < 2:
+                grid.append(row)
+                del A, b, xt
+                torch.cuda.empty_cache()
+                continue
             row["mixed_vs_fp64_rel_diff"] = float(torch.linalg.norm(xs["mixed_splitbf16"] - xs["fp64"]) /
                                                   torch.linalg.norm(xs["fp64"]))
             if f"{m}x{n}" in oracle_shapes:
