@@ -10,14 +10,28 @@
 // FP32-level accuracy from BF16 tensor cores.
 //
 // Kernel structure (one CTA per 128 x BN output tile, 6 warps):
-//   warp 0      TMA producer: 3-D tensor loads (K x rows x slice) of 128 x 64
-//               BF16 tiles, 128-byte swizzle, into a 4-stage ring guarded by
+//   warp 0      TMA producer: 3-D tensor loads (K x rows x slices) of BF16
+//               tiles, 128-byte swizzle, into a ring of stages guarded by
 //               mbarriers (full: bytes landed; empty: MMAs done reading).
+//               Long K (at least 4 K tiles per CTA): K-major - per K step one
+//               load of every slice of the 128 x 64 A tile and one of every
+//               slice of the BN x 64 B tile, so each slice tile is read once
+//               (2-4 stages).  Short K: product-major - per product and K
+//               step one A slice tile and one B slice tile (4 stages): the
+//               first MMA waits for one small stage, and re-reads of the few
+//               tiles come from L2.
 //   warp 1      allocates TMEM; one thread issues tcgen05.mma kind::f16
-//               (M = 128, N = BN, K = 16 per instruction) and tcgen05.commit.
-//   warps 2-5   epilogue: tcgen05.ld the FP32 accumulator (warp w reads TMEM
+//               (M = 128, N = BN, K = 16 per instruction) for every product
+//               of every stage, then tcgen05.commit.  The leading product
+//               x_1 y_1 accumulates in one TMEM accumulator and the smaller
+//               ones in a second, so their low-order bits are not rounded
+//               away against the leading product's running sum at every K
+//               step; the epilogue adds the two once.
+//   warps 2-5   epilogue: tcgen05.ld the FP32 accumulators (warp w reads TMEM
 //               lanes 32*(w%4) .. +31), combine into C in FP64 (or write FP32
-//               split-K partials).
+//               split-K partials).  Each FP64 instruction takes a warp about
+//               64 cycles here, so the epilogue spends as few as it can: the
+//               C -= update is one conversion and one subtraction per entry.
 // Every mbarrier wait is bounded (about 2 s by %globaltimer); on timeout the
 // kernel raises an error flag, stops issuing work, drains what it issued and
 // frees its TMEM.
@@ -36,13 +50,17 @@ namespace {
 
 constexpr int TC_BM = 128;
 constexpr int TC_BK = 64;          // one 128-byte swizzle row of BF16
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_STAGES = 4;
+constexpr size_t TC_SMEM_LIMIT = 225 * 1024;   // dynamic shared memory a CTA may take
 constexpr int TC_THREADS = 192;
 constexpr uint32_t A_TILE_BYTES = TC_BM * TC_BK * 2;
 
 struct TcParams {
     int M, N, K;
     int ktiles_per_split;
+    int nsplit;              // slices per operand
+    int kmajor;              // 1: every slice per K step (box depth nsplit); 0: one product per stage
+    int stages;              // ring depth
     int npairs;
     int pair_a[6], pair_b[6];
     double *C; int64_t ldc;
@@ -160,21 +178,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     constexpr uint32_t B_TILE_BYTES = BN * TC_BK * 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int NS = p.stages;
+    const int depth = p.kmajor ? p.nsplit : 1;   // slice tiles per operand in a stage
+    const uint32_t a_stage = (uint32_t)depth * A_TILE_BYTES, b_stage = (uint32_t)depth * B_TILE_BYTES;
     uint8_t *sA = smem;
-    uint8_t *sB = sA + TC_STAGES * A_TILE_BYTES;
-    uint64_t *bars = (uint64_t *)(sB + TC_STAGES * B_TILE_BYTES);   // full[S], empty[S], done
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * TC_STAGES + 1);
+    uint8_t *sB = sA + NS * a_stage;
+    uint64_t *bars = (uint64_t *)(sB + NS * b_stage);   // full[S], empty[S], done
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * NS + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN, z = blockIdx.z;
     const int ktiles = (p.K + TC_BK - 1) / TC_BK;
     const int kt0 = z * p.ktiles_per_split;
     const int nk = max(0, min(ktiles, kt0 + p.ktiles_per_split) - kt0);
-    const int total = nk * p.npairs;
-    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES), done = smem_u32(bars + 2 * TC_STAGES);
+    const int total = p.kmajor ? nk : nk * p.npairs;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + NS), done = smem_u32(bars + 2 * NS);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < TC_STAGES; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
@@ -182,9 +203,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    // two accumulators (leading product, the others) when there are several products
+    const uint32_t tcols = p.npairs > 1 ? 2 * BN : BN;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN));
+                     "r"(tcols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -196,31 +219,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (lane == 0) {
             int issued = 0;
             for (int it = 0; it < total; ++it) {
-                const int s = it % TC_STAGES, r = it / TC_STAGES;
+                const int s = it % NS, r = it / NS;
                 if (!mbar_wait(empty0 + 8 * s, (uint32_t)((r & 1) ^ 1), p.err)) break;
-                const int pair = it / nk, kt = kt0 + it % nk;
-                mbar_expect_tx(full0 + 8 * s, A_TILE_BYTES + B_TILE_BYTES);
-                tma_load_3d(smem_u32(sA + s * A_TILE_BYTES), &tmA, kt * TC_BK, m0, p.pair_a[pair], full0 + 8 * s);
-                tma_load_3d(smem_u32(sB + s * B_TILE_BYTES), &tmB, kt * TC_BK, n0, p.pair_b[pair], full0 + 8 * s);
+                const int pair = p.kmajor ? 0 : it / nk, kt = kt0 + (p.kmajor ? it : it % nk);
+                mbar_expect_tx(full0 + 8 * s, a_stage + b_stage);
+                tma_load_3d(smem_u32(sA + s * a_stage), &tmA, kt * TC_BK, m0, p.kmajor ? 0 : p.pair_a[pair],
+                            full0 + 8 * s);
+                tma_load_3d(smem_u32(sB + s * b_stage), &tmB, kt * TC_BK, n0, p.kmajor ? 0 : p.pair_b[pair],
+                            full0 + 8 * s);
                 issued = it + 1;
             }
             // after an abort, let the loads already issued land before the CTA exits
             if (issued < total)
-                for (int it = max(0, issued - TC_STAGES); it < issued; ++it)
-                    mbar_wait(full0 + 8 * (it % TC_STAGES), (uint32_t)((it / TC_STAGES) & 1), p.err);
+                for (int it = max(0, issued - NS); it < issued; ++it)
+                    mbar_wait(full0 + 8 * (it % NS), (uint32_t)((it / NS) & 1), p.err);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             const uint32_t idesc = idesc_bf16(TC_BM, BN);
             for (int it = 0; it < total; ++it) {
-                const int s = it % TC_STAGES, r = it / TC_STAGES;
+                const int s = it % NS, r = it / NS;
                 if (!mbar_wait(full0 + 8 * s, (uint32_t)(r & 1), p.err)) break;
                 tc_fence_after();
-                const uint64_t ad = sw128_desc(smem_u32(sA + s * A_TILE_BYTES));
-                const uint64_t bd = sw128_desc(smem_u32(sB + s * B_TILE_BYTES));
+                // the products of this stage: the smaller ones into the second
+                // accumulator, the leading one (last in the list) into the first
+                const int q0 = p.kmajor ? 0 : it / nk, q1 = p.kmajor ? p.npairs : q0 + 1;
+                const int kstep = p.kmajor ? it : it % nk;
+                for (int q = q0; q < q1; ++q) {
+                    const int ai = p.kmajor ? p.pair_a[q] : 0, bi = p.kmajor ? p.pair_b[q] : 0;
+                    const uint64_t ad = sw128_desc(smem_u32(sA + s * a_stage + ai * A_TILE_BYTES));
+                    const uint64_t bd = sw128_desc(smem_u32(sB + s * b_stage + bi * B_TILE_BYTES));
+                    const bool lead = q == p.npairs - 1;
+                    const uint32_t acc_addr = lead ? tmem : tmem + (uint32_t)BN;
+                    // the first MMA into each accumulator overwrites it
+                    const bool first = kstep == 0 && (lead || q == 0);
 #pragma unroll
-                for (int kk = 0; kk < TC_BK / 16; ++kk)
-                    mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < TC_BK / 16; ++kk)
+                        mma_bf16(acc_addr, ad + 2 * kk, bd + 2 * kk, idesc, (!first || kk > 0) ? 1u : 0u);
+                }
                 mma_commit(empty0 + 8 * s);
             }
             mma_commit(done);   // arrives once every MMA issued above has completed
@@ -237,8 +273,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // of C is latency-bound at a few GB/s per SM).
 #pragma unroll 1
         for (int chunk = 0; chunk < BN / 32; ++chunk) {
-            uint32_t v[32];
+            uint32_t v[32], v2[32];
             if (total > 0) tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(chunk * 32), v);
+            if (total > 0 && p.npairs > 1)
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + chunk * 32), v2);
             if (!ok || m >= p.M) continue;
             const int nbase = n0 + chunk * 32;
             const int cnt = min(32, p.N - nbase);
@@ -247,18 +285,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 float *pp = p.partial + (size_t)z * p.M * p.N + m + (size_t)nbase * p.M;
 #pragma unroll
                 for (int c = 0; c < 32; ++c)
-                    if (c < cnt) pp[(size_t)c * p.M] = (total > 0) ? __uint_as_float(v[c]) : 0.0f;
+                    if (c < cnt)
+                        pp[(size_t)c * p.M] = (total > 0) ? __uint_as_float(v[c]) +
+                                                                (p.npairs > 1 ? __uint_as_float(v2[c]) : 0.0f)
+                                                          : 0.0f;
             } else {
                 double *cp = p.C + m + (size_t)nbase * p.ldc;
                 double cv[32];
 #pragma unroll
                 for (int c = 0; c < 32; ++c) cv[c] = (p.beta != 0.0 && c < cnt) ? cp[(size_t)c * p.ldc] : 0.0;
+                const bool sub = p.beta == 1.0 && p.alpha == -1.0, plain = p.beta == 0.0 && p.alpha == 1.0;
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
                     if (c < cnt) {
-                        const double d = (total > 0) ? (double)__uint_as_float(v[c]) : 0.0;
-                        double out = p.alpha * d;
-                        if (p.beta != 0.0) out = fma(p.beta, cv[c], out);
+                        const float f = (total > 0) ? __uint_as_float(v[c]) + (p.npairs > 1 ? __uint_as_float(v2[c]) : 0.0f)
+                                                    : 0.0f;
+                        const double d = (double)f;
+                        double out;
+                        if (sub) out = cv[c] - d;
+                        else if (plain) out = d;
+                        else if (p.beta == 0.0) out = p.alpha * d;
+                        else out = fma(p.beta, cv[c], p.alpha * d);
                         cp[(size_t)c * p.ldc] = out;
                     }
                 }
@@ -269,7 +316,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
     }
 }
 
@@ -285,8 +332,10 @@ __global__ void __launch_bounds__(kThreads) tc_reduce_kernel(int M, int N, int S
         double s = 0.0;
         for (int z = 0; z < S; ++z) s += (double)P[(size_t)z * total + e];
         double *cp = C + m + (int64_t)n * ldc;
-        double out = alpha * s;
-        if (beta != 0.0) out = fma(beta, *cp, out);
+        double out;
+        if (beta == 0.0) out = (alpha == 1.0) ? s : alpha * s;
+        else if (beta == 1.0 && alpha == -1.0) out = *cp - s;
+        else out = fma(beta, *cp, alpha * s);
         *cp = out;
     }
 }
@@ -386,20 +435,29 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D map over BF16 slices: dims (K, rows, slices), row stride ldd elements.
-bool make_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, int slices, int64_t ldd, int box_rows) {
+// 3-D map over BF16 slices: dims (K, rows, slices), row stride ldd elements;
+// one box holds box_slices slices of a 64 x box_rows tile.
+bool make_map(CUtensorMap *map, const void *base, int64_t K, int64_t rows, int slices, int64_t ldd, int box_rows,
+              int box_slices) {
     auto enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slices};
     cuuint64_t strides[2] = {(cuuint64_t)ldd * 2, (cuuint64_t)ldd * (cuuint64_t)rows * 2};
-    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-size_t tc_smem_bytes(int BN) { return 1024 + TC_STAGES * (A_TILE_BYTES + (size_t)BN * TC_BK * 2) + 256; }
+// depth: slice tiles per operand in a stage (nsplit when K-major, else 1)
+size_t tc_stage_bytes(int BN, int depth) { return (size_t)depth * (A_TILE_BYTES + (size_t)BN * TC_BK * 2); }
+// Deepest ring (at most TC_MAX_STAGES) that fits the shared-memory limit.
+int tc_stages(int BN, int depth) {
+    const size_t fixed = 1024 + 256;
+    return (int)std::min<size_t>(TC_MAX_STAGES, (TC_SMEM_LIMIT - fixed) / tc_stage_bytes(BN, depth));
+}
+size_t tc_smem_bytes(int BN, int depth) { return 1024 + tc_stages(BN, depth) * tc_stage_bytes(BN, depth) + 256; }
 
 int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
 
@@ -460,6 +518,10 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
     TcParams p;
     p.M = (int)op.M; p.N = (int)op.N; p.K = (int)K;
     p.ktiles_per_split = per;
+    p.nsplit = op.nsplit;
+    p.kmajor = (op.nsplit > 1 && per >= 4) ? 1 : 0;
+    const int depth = p.kmajor ? op.nsplit : 1;
+    p.stages = tc_stages(BN, depth);
     static const int pa[6] = {0, 0, 1, 0, 1, 2}, pb[6] = {0, 1, 0, 2, 1, 0};
     p.npairs = op.nsplit == 1 ? 1 : (op.nsplit == 2 ? 3 : 6);
     // smaller products first, the leading one last
@@ -472,16 +534,18 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
     p.err = sc.err;
 
     CUtensorMap mA, mB;
-    if (!make_map(&mA, As, K, op.M, op.nsplit, ldk, TC_BM) || !make_map(&mB, Bs, K, op.N, op.nsplit, ldk, BN))
+    if (!make_map(&mA, As, K, op.M, op.nsplit, ldk, TC_BM, depth) || !make_map(&mB, Bs, K, op.N, op.nsplit, ldk, BN, depth))
         return GBQR_ECUDA;
-    const size_t smem = tc_smem_bytes(BN);
-    // per device and tile width, once (server workers launch from several threads)
+    const size_t smem = tc_smem_bytes(BN, depth);
+    // per device and tile width, once (server workers launch from several
+    // threads): allow the limit, each launch asks for what its ring needs
     static std::atomic<bool> attr[64][2];
     const int bi = BN == 128 ? 1 : 0;
     const bool cached = ex.device >= 0 && ex.device < 64;
     if (!cached || !attr[ex.device][bi].load(std::memory_order_acquire)) {
-        cudaError_t e = (BN == 128) ? cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                                    : cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int lim = (int)TC_SMEM_LIMIT;
+        cudaError_t e = (BN == 128) ? cudaFuncSetAttribute(tc_gemm_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)
+                                    : cudaFuncSetAttribute(tc_gemm_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         if (e != cudaSuccess) return GBQR_ECUDA;
         if (cached) attr[ex.device][bi].store(true, std::memory_order_release);
     }
@@ -490,7 +554,7 @@ gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc) {
     if (BN == 128) tc_gemm_kernel<128><<<grid, TC_THREADS, smem, ex.stream>>>(mA, mB, p);
     else tc_gemm_kernel<64><<<grid, TC_THREADS, smem, ex.stream>>>(mA, mB, p);
     const double pairs_flops = 2.0 * (double)op.M * op.N * K * p.npairs;
-    TRY_ST(trace_end(ex, FAM_TC_GEMM, pairs_flops, 2.0 * p.npairs * ((double)op.M + op.N) * K));
+    TRY_ST(trace_end(ex, FAM_TC_GEMM, pairs_flops, 2.0 * op.nsplit * ((double)op.M + op.N) * K));   // each slice once
     if (S > 1) {
         trace_begin(ex, FAM_OTHER);
         const int64_t total = op.M * op.N;
