@@ -392,7 +392,11 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
 // masked), T = its kernel.  Two passes over the rows in chunks of H rows,
 // each chunk copied asynchronously into one of two stages while the other
 // stage is computed on: W = V^T C (each thread accumulates its W entries
-// over every row), then W = T^T W, then C -= V W.
+// over every row), then W = T^T W, then C -= V W.  In FP64 the FMAs bound
+// the task; in FP32 (64x the FMA rate) shared-memory reads would, so there
+// each thread of pass 1 accumulates a 2 x (kMaxOut/2) block of W (one
+// shared load per FMA instead of two), and in pass 2 each thread keeps its
+// row of V in registers and reads W by broadcast.
 template <int MaxB, class Real>
 __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, int c0, int c1, Real *sm) {
     constexpr int kMaxOut = (MaxB * kUpdCols + kThreads - 1) / kThreads;   // W entries per thread
@@ -433,6 +437,15 @@ __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, 
     Real acc[kMaxOut];
 #pragma unroll
     for (int q = 0; q < kMaxOut; ++q) acc[q] = Real(0);
+    // FP32 pass-1 blocking: MaxB / 2 pairs of V columns x kUpdCols / kCr
+    // groups of C columns = kThreads blocks
+    constexpr bool kFp32 = sizeof(Real) == 4;
+    constexpr int kCr = kMaxOut / 2;
+    static_assert(!kFp32 || (MaxB / 2) * (kUpdCols / kCr) == kThreads, "FP32 pass-1 blocking");
+    const int jb = tid % (MaxB / 2), cb = tid / (MaxB / 2);
+    Real acc2[2][kCr];
+#pragma unroll
+    for (int q = 0; q < kCr; ++q) { acc2[0][q] = Real(0); acc2[1][q] = Real(0); }
     for (int ch = 0; ch < nch; ++ch) {
         if (ch + 1 < nch) { issue(ch + 1, true); cp_wait<1>(); }
         else cp_wait<0>();
@@ -440,24 +453,48 @@ __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, 
         const int hc = min(H, mr - ch * H), st = ch & 1;
         Real *Vc = Vs + st * vst, *Cc = Cs + st * cst;
         if (ch == 0) { mask_top(Vc, hc); __syncthreads(); }
+        if constexpr (kFp32) {
+            // columns j of this thread: 2 jb, 2 jb + 1; columns c: kCr cb + q
+            const Real *v0 = Vc + (2 * jb) * ldc, *v1 = v0 + ldc, *cp = Cc + (kCr * cb) * ldc;
+            for (int r = 0; r < hc; ++r) {
+                const Real a0 = v0[r], a1 = v1[r];
 #pragma unroll
-        for (int q = 0; q < kMaxOut; ++q) {
-            const int o = tid + q * kThreads;
-            if (o < nout) {
-                const int j = o % w, c = o / w;
-                const Real *vp = Vc + j * ldc, *cp = Cc + c * ldc;
-                Real a = acc[q];
-                for (int r = 0; r < hc; ++r) a = rfma(vp[r], cp[r], a);
-                acc[q] = a;
+                for (int q = 0; q < kCr; ++q) {
+                    const Real x = cp[r + q * ldc];
+                    acc2[0][q] = rfma(a0, x, acc2[0][q]);
+                    acc2[1][q] = rfma(a1, x, acc2[1][q]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < kMaxOut; ++q) {
+                const int o = tid + q * kThreads;
+                if (o < nout) {
+                    const int j = o % w, c = o / w;
+                    const Real *vp = Vc + j * ldc, *cp = Cc + c * ldc;
+                    Real a = acc[q];
+                    for (int r = 0; r < hc; ++r) a = rfma(vp[r], cp[r], a);
+                    acc[q] = a;
+                }
             }
         }
         __syncthreads();                 // the stage is reloaded two chunks on
     }
     issue(0, true);                      // pass 2's first chunk, under the T^T W product
+    if constexpr (kFp32) {
 #pragma unroll
-    for (int q = 0; q < kMaxOut; ++q) {
-        const int o = tid + q * kThreads;
-        if (o < nout) Ws[o % w + (o / w) * b] = acc[q];
+        for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+            for (int q = 0; q < kCr; ++q) {
+                const int j = 2 * jb + jj, c = kCr * cb + q;
+                if (j < w && c < cw) Ws[j + c * b] = acc2[jj][q];
+            }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kMaxOut; ++q) {
+            const int o = tid + q * kThreads;
+            if (o < nout) Ws[o % w + (o / w) * b] = acc[q];
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -483,11 +520,29 @@ __device__ void update_task(const BParams<Real> &p, const BMat<Real> &M, int k, 
         const int r0 = ch * H, hc = min(H, mr - r0), st = ch & 1;
         Real *Vc = Vs + st * vst, *Cc = Cs + st * cst;
         if (ch == 0) { mask_top(Vc, hc); __syncthreads(); }
-        for (int e = tid; e < hc * cw; e += nthr) {
-            const int c = e / hc, r = e - c * hc;
-            Real s = Real(0);
-            for (int j = 0; j < w; ++j) s = rfma(Vc[r + j * ldc], Ws[j + c * b], s);
-            C[r0 + r + (int64_t)c * lda] = Cc[r + c * ldc] - s;
+        if constexpr (kFp32) {
+            // thread: row r (consecutive across lanes: coalesced C), every
+            // groups-th column from g; V(r, :) in registers, W by broadcast
+            const int nr = min(H, nthr), groups = nthr / nr;
+            for (int r = tid % nr; r < hc; r += nr) {
+                Real vr[MaxB];
+#pragma unroll
+                for (int j = 0; j < MaxB; ++j) vr[j] = (j < w) ? Vc[r + j * ldc] : Real(0);
+                for (int c = tid / nr; c < cw; c += groups) {
+                    const Real *wc = Ws + c * b;
+                    Real s = Real(0);
+#pragma unroll
+                    for (int j = 0; j < MaxB; ++j) s = rfma(vr[j], (j < w) ? wc[j] : Real(0), s);
+                    C[r0 + r + (int64_t)c * lda] = Cc[r + c * ldc] - s;
+                }
+            }
+        } else {
+            for (int e = tid; e < hc * cw; e += nthr) {
+                const int c = e / hc, r = e - c * hc;
+                Real s = Real(0);
+                for (int j = 0; j < w; ++j) s = rfma(Vc[r + j * ldc], Ws[j + c * b], s);
+                C[r0 + r + (int64_t)c * lda] = Cc[r + c * ldc] - s;
+            }
         }
         __syncthreads();
     }
