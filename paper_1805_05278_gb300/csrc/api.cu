@@ -673,6 +673,10 @@ gbqr_status apply_q_any(Work &w, bool trans, int64_t m, int64_t n, const double 
     // the diagonal blocks of T (those of consecutive reflectors).
     const int64_t pb = (layout == GBQR_T_FULL) ? std::min<int64_t>(kDefaultPanel, n) : nb;
     const int64_t npan = (n + pb - 1) / pb;
+    if (nrhs == 1 && !form_q_structure && pb <= kApplyVecMaxW && (size_t)(2 * pb) <= w.n_M && w.tcs.err)
+        // one vector: every panel in one persistent launch
+        return apply_vec(w.ex, trans, m, n, VR, lda, T, ldt, layout == GBQR_T_FULL, pb, B, w.M1, w.n_M,
+                         w.gs.partial, w.gs.partial_elems, w.gs.counters, w.gs.ncounters, w.tcs.err);
     for (int64_t q = 0; q < npan; ++q) {
         const int64_t k = trans ? q : npan - 1 - q;
         const int64_t j0 = k * pb, wd = std::min<int64_t>(pb, n - j0);

@@ -199,6 +199,16 @@ gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool
 gbqr_status frob2(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, double *colsq, double *out);
 // y = a x + b y
 gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y);
+constexpr int kApplyVecMaxW = 256;   // widest panel apply_vec takes
+// x <- Q^T x (trans) or Q x for one vector x (m), Q from the packed V of
+// VR (lda) and the panel kernels of T (ldt; tfull: T is the full n x n
+// kernel and its diagonal pb x pb blocks are used), panels of width pb: one
+// persistent launch.  y2: 2 pb doubles; partial: >= ceil(m / rows per
+// item) pb doubles; counters: 5, zero on entry, left zero; timeout: the
+// context's device flag, raised if a bounded wait runs out.
+gbqr_status apply_vec(const Exec &ex, bool trans, int64_t m, int64_t n, const double *VR, int64_t lda,
+                      const double *T, int64_t ldt, bool tfull, int64_t pb, double *x, double *y2, size_t ny,
+                      double *partial, size_t partial_elems, unsigned *counters, size_t ncounters, int *timeout);
 
 // ------------------------------------------------------------ tuner cache
 // Context accessors for the tuner (the context's layout lives in api.cu).

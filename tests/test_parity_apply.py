@@ -63,6 +63,42 @@ def test_apply_and_form_q(gb, ctx, orc, m, n, seed, layout_name):
     assert np.linalg.norm(q.T @ q - np.eye(n)) <= _gpu.TOL_BACKWARD
 
 
+@pytest.mark.parametrize("m,n,nb,layout_name", [
+    (1000, 77, 32, "panel"),      # ragged last panel, one CTA per few chunks
+    (40000, 300, 128, "panel"),   # ~125 CTAs: two levels of the reduction tree
+    (20000, 512, 256, "panel"),   # widest panel the one-vector kernel takes
+    (5000, 300, 0, "full"),       # diagonal blocks of the full T
+    (64, 64, 16, "panel"),        # square: the last panels span a single chunk
+    (50, 1, 1, "panel"),
+])
+def test_apply_one_vector(gb, ctx, orc, m, n, nb, layout_name):
+    """Q^T b and Q b of a single vector (the one-launch-per-panel path) against
+    the oracle, for both directions, ragged panels and multi-level trees."""
+    import torch
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    nb = nb if layout == gb.GBQR_T_PANEL else n
+    a = workloads.gaussian(m, n, 40 + n)
+    b = workloads.gaussian(m, 1, 41 + n)
+    vr_o, tau_o = orc.house_qr(a)
+    A = _gpu.device_matrix(a)
+    T = _gpu.t_buffer(n, layout, nb)
+    ctx.factor(A, T, layout, gb.opts(panel_nb=nb) if layout == gb.GBQR_T_PANEL else None)
+    scale = np.linalg.norm(b)
+    B = _gpu.device_matrix(b)
+    ctx.apply_qt(A, T, B, layout, nb)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(gb.to_numpy(B) - orc.apply_qt(vr_o, tau_o, b))) / scale <= TOL_APPLY
+    B2 = _gpu.device_matrix(b)
+    ctx.apply_q(A, T, B2, layout, nb)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(gb.to_numpy(B2) - orc.apply_q(vr_o, tau_o, b))) / scale <= TOL_APPLY
+    # deterministic: a second application gives the same bits
+    B3 = _gpu.device_matrix(b)
+    ctx.apply_q(A, T, B3, layout, nb)
+    torch.cuda.synchronize()
+    assert torch.equal(B2, B3)
+
+
 @pytest.mark.parametrize("m,n,seed", [(1024, 128, 0), (777, 100, 5), (256, 256, 6), (3000, 17, 7)])
 def test_ls_solve(gb, ctx, orc, m, n, seed):
     import torch
