@@ -102,6 +102,9 @@ struct TcScratch {
     int *err = nullptr;                       // device flag raised on a timed-out wait
 };
 size_t tc_gemm_scratch_bytes(int64_t M, int64_t N, int64_t K, int num_sms);
+// The driver's cuTensorMapEncodeTiled (as a PFN_cuTensorMapEncodeTiled_v12000),
+// or null when the driver does not provide it.
+void *tensor_map_encoder();
 gbqr_status tc_gemm(const Exec &ex, const TcGemmOp &op, const TcScratch &sc);
 
 // ------------------------------------------------------------------ TSQR

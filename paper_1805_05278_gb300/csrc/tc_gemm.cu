@@ -463,6 +463,8 @@ int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
 
 }  // namespace
 
+void *tensor_map_encoder() { return (void *)encode_fn(); }
+
 size_t tc_gemm_scratch_bytes(int64_t M, int64_t N, int64_t K, int num_sms) {
     const int64_t ldk = pad8(std::max<int64_t>(K, 1));
     size_t b = 0;

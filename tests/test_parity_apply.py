@@ -70,6 +70,11 @@ def test_apply_and_form_q(gb, ctx, orc, m, n, seed, layout_name):
     (5000, 300, 0, "full"),       # diagonal blocks of the full T
     (64, 64, 16, "panel"),        # square: the last panels span a single chunk
     (50, 1, 1, "panel"),
+    (1001, 77, 32, "panel"),      # odd leading dimension: per-lane loads instead of tensor boxes
+    (1000, 77, 33, "panel"),      # odd panel width and ldt: T read from global memory
+    (3000, 200, 64, "panel"),     # narrower boxes, deeper ring
+    (1024, 128, 128, "panel"),    # one panel, one chunk per item: the item's last chunk in ring slot 0
+    (16384, 128, 128, "panel"),   # four chunks per item in a three-slot ring
 ])
 def test_apply_one_vector(gb, ctx, orc, m, n, nb, layout_name):
     """Q^T b and Q b of a single vector (the one-launch-per-panel path) against
