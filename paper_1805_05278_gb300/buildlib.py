@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libgbqr.so")
 ROOT = os.path.dirname(HERE)
 
-SOURCES = ["api.cu", "gemm.cu", "tsqr.cu", "aux_kernels.cu", "probe.cu", "noalloc.cu", "tc_gemm.cu", "server.cu", "tune.cu", "batched.cu", "applyvec.cu"]
+SOURCES = ["api.cu", "gemm.cu", "tsqr.cu", "aux_kernels.cu", "probe.cu", "noalloc.cu", "tc_gemm.cu", "server.cu", "tune.cu", "batched.cu", "applyvec.cu", "trsvchain.cu"]
 HEADERS = ["common.cuh", "tsqr_dev.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -1041,7 +1041,13 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     // once, and every block step becomes a small matrix-vector product
     const double *dinv = (prec != GBQR_FP64) ? w.dinv : nullptr;
     if (dinv) TRY(trsv_block_inverses(w.ex, n, w.bigA, m, w.dinv, &di->rankdef));
-    TRY(trsv_upper(w.ex, n, w.bigA, m, x, &di->rankdef, dinv));
+    // with the block inverses, each solve is one launch of the block chain
+    auto solve_r = [&](bool trans, double *v) -> gbqr_status {
+        if (dinv) return trsv_chain(w.ex, trans, n, w.bigA, m, v, dinv, w.gs.counters, w.gs.ncounters, &di->timeout);
+        return trans ? trsv_upper_t(w.ex, n, w.bigA, m, v, &di->rankdef, dinv)
+                     : trsv_upper(w.ex, n, w.bigA, m, v, &di->rankdef, dinv);
+    };
+    TRY(solve_r(false, x));
     // Refinement on the augmented system K [r; x] = [b; 0], K = [I A; A^T 0],
     // with FP64 residuals.  The mixed QR solves K approximately (M^{-1}):
     //   h = R^{-T} g,  d = Q^T f,  dx = R^{-1} (d(0:n) - h),  dr = Q [h; d(n:m)].
@@ -1087,11 +1093,11 @@ gbqr_status gbqr_ls_solve(gbqr_ctx *cx, int64_t m, int64_t n, const double *A, i
     if (prec != GBQR_FP64) {
         auto precond = [&](double *fv, double *gv, double *dxv) -> gbqr_status {
             // in (fv, gv); out: dr in fv, dx in dxv; gv is overwritten (h)
-            TRY(trsv_upper_t(w.ex, n, w.bigA, m, gv, &di->rankdef, dinv));
+            TRY(solve_r(true, gv));
             TRY(apply_q_any(w, true, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, fv, m, false));
             TRY(copy_matrix(w.ex, n, 1, fv, n, dxv, n));
             TRY(axpby(w.ex, n, -1.0, gv, 1.0, dxv));
-            TRY(trsv_upper(w.ex, n, w.bigA, m, dxv, &di->rankdef, dinv));
+            TRY(solve_r(false, dxv));
             TRY(copy_matrix(w.ex, n, 1, gv, n, fv, n));
             return apply_q_any(w, false, m, n, w.bigA, m, w.bigT, nb, GBQR_T_PANEL, nb, 1, fv, m, false);
         };

@@ -51,6 +51,7 @@ constexpr int kMaxStages = 4;
 static_assert(kMaxW % (32 * kWarps) == 0 && kMaxW <= kThreads, "one column of w per thread");
 static_assert(kWarps * kChunkL <= kTiles * kMaxW, "phase A partials fit the T-product buffer");
 static_assert(kTmaMaxW * (kTmaMaxW + 2) * 8 <= kRingBytes, "staged T fits the ring");
+static_assert(kTmaMaxW <= 32 * (kWarps - 1), "the warp staging T is not one of those reading the group sums");
 
 enum { kTicket = 0, kArrive = 1, kReady = 2, kDone = 3, kAbort = 4, kGroupCtr = 5, kNumCounters = kGroupCtr + kMaxGroups };
 
@@ -445,17 +446,14 @@ __device__ void t_product(const ApplyVec &p, const Stage &st, Smem &sm, const do
 
 // Copy T_s's upper triangle into shared memory: column c (rows 0..c) at
 // Ts + c tstride, one bulk copy per column of its 16-byte pairs, the odd last
-// entry of a column by a plain load.  Warp 0 issues; completes on sm.tbar.
+// entry of a column by a plain load.  One warp issues; completes on sm.tbar.
 __device__ void t_stage_issue(const ApplyVec &p, const Stage &st, Smem &sm, double *Ts) {
     const int lane = threadIdx.x & 31, wk = st.wk;
     const double *Tk = panel_T(p, st.jk);
     const uint32_t bar = smem_u32(&sm.tbar);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic reads of the ring came before
-    if (lane == 0) {
-        uint32_t bytes = 0;
-        for (int c = 0; c < wk; ++c) bytes += (uint32_t)((c + 1) / 2) * 16;
-        mbar_expect_tx(bar, bytes);
-    }
+    // sum over columns of floor((c + 1) / 2) pairs = floor(wk^2 / 4)
+    if (lane == 0) mbar_expect_tx(bar, (uint32_t)(wk * wk / 4) * 16);
     __syncwarp();
     for (int c = lane; c < wk; c += 32) {
         const uint32_t pairs = (uint32_t)(c + 1) / 2;
@@ -500,9 +498,10 @@ __device__ void arrive_item(const ApplyVec &p, const Stage &st, Smem &sm, int s,
     }
     __syncthreads();
     if (!sm.flag) return;
-    // the stage's last arriver: T on its way while the group sums are read
+    // the stage's last arriver: T on its way (the last warp issues) while
+    // warps 0-3 read the group sums
     const bool staged = p.tsm && Ts;
-    if (staged && threadIdx.x < 32) t_stage_issue(p, st, sm, Ts);
+    if (staged && (tid >> 5) == kWarps - 1) t_stage_issue(p, st, sm, Ts);
     if (tid < wk) {
         const double *src = p.gsum + tid;
         double v[kMaxGroups];

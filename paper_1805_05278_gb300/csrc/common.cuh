@@ -202,6 +202,12 @@ gbqr_status trmv_upper(const Exec &ex, int k, const double *T, int64_t ldt, bool
 gbqr_status frob2(const Exec &ex, int64_t m, int64_t n, const double *A, int64_t lda, double *colsq, double *out);
 // y = a x + b y
 gbqr_status axpby(const Exec &ex, int64_t n, double a, const double *x, double b, double *y);
+// R x = c (trans: R^T x = c) for one vector with the inverses of R's 64 x 64
+// diagonal blocks in Dinv (trsv_block_inverses): one persistent launch, the
+// blocks solved in order and published through counters (4, zero on entry,
+// left zero); timeout: the context's device flag for a bounded wait.
+gbqr_status trsv_chain(const Exec &ex, bool trans, int64_t n, const double *R, int64_t ldr, double *x,
+                       const double *Dinv, unsigned *counters, size_t ncounters, int *timeout);
 constexpr int kApplyVecMaxW = 256;   // widest panel apply_vec takes
 // x <- Q^T x (trans) or Q x for one vector x (m), Q from the packed V of
 // VR (lda) and the panel kernels of T (ldt; tfull: T is the full n x n
