@@ -505,6 +505,17 @@ GBQR_API gbqr_status gbqr_selftest_wait_timeout(int device, int *completed);
  * Errors: EINVAL, ENOMEM, ECUDA. */
 GBQR_API gbqr_status gbqr_selftest_batched_wait(int device, int wait_ms, int *completed);
 
+/* Failure-detection self-test of the persistent triangular-solve chain (and,
+ * by the same wait, of the one-vector Q application): one CTA is handed the
+ * second block of a two-block solve, so the block it waits for is never
+ * solved and its bounded wait (wait_ms, 1..10000) must run out, raise the
+ * abort and timeout flags, and return with the launch's counters reset.
+ * Expected: GBQR_ETIMEOUT with *completed = 0 (no block solved), and the
+ * device still usable.  The paper has no counterpart.  Synchronous;
+ * allocates about 200 KB.  Errors: EINVAL, ENOMEM, ECUDA (also when the
+ * counters were not left zero). */
+GBQR_API gbqr_status gbqr_selftest_chain_wait(int device, int wait_ms, int *completed);
+
 /* Human-readable name of a status. */
 GBQR_API const char *gbqr_strerror(gbqr_status s);
 

@@ -113,6 +113,7 @@ SIGNATURES = {
     "gbqr_fp64_peak": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "gbqr_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_selftest_batched_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "gbqr_selftest_chain_wait": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "gbqr_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

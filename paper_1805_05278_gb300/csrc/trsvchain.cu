@@ -251,3 +251,52 @@ gbqr_status trsv_chain(const Exec &ex, bool trans, int64_t n, const double *R, i
 }
 
 }  // namespace gbqr
+
+// Failure-detection self-test: one CTA is handed the second block of a
+// two-block solve (the ticket counter starts at 1), so the first block is
+// never solved and its bounded wait must run out.
+extern "C" GBQR_API gbqr_status gbqr_selftest_chain_wait(int device, int wait_ms, int *completed) {
+    using namespace gbqr;
+    if (!completed || wait_ms < 1 || wait_ms > 10000) return GBQR_EINVAL;
+    *completed = -1;
+    if (cudaSetDevice(device) != cudaSuccess) return GBQR_ECUDA;
+    const int64_t n = 2 * B;
+    // [R (n x n) | Dinv (2 blocks) | x (n) | counters (4) + timeout flag]
+    const size_t nR = (size_t)n * n, nD = 2 * (size_t)B * B;
+    const size_t bytes = 8 * (nR + nD + n) + 64;
+    char *d = nullptr;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return GBQR_ENOMEM; }
+    double *R = reinterpret_cast<double *>(d), *Dv = R + nR, *x = Dv + nD;
+    unsigned *ctr = reinterpret_cast<unsigned *>(x + n);
+    int *flag = reinterpret_cast<int *>(ctr + kNumCounters);
+    gbqr_status st = GBQR_OK;
+    double xh[2 * B];
+    for (int i = 0; i < n; ++i) xh[i] = 1.0;
+    const unsigned one = 1u;
+    if (cudaMemset(d, 0, bytes) != cudaSuccess || cudaMemcpy(x, xh, sizeof xh, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ctr + kTicket, &one, sizeof one, cudaMemcpyHostToDevice) != cudaSuccess)
+        st = GBQR_ECUDA;
+    int h = 0;
+    unsigned left[kNumCounters] = {1u, 1u, 1u, 1u};
+    if (st == GBQR_OK) {
+        Chain p;
+        p.n = n; p.ldr = n; p.R = R; p.Dinv = Dv; p.x = x;
+        p.nblk = 2; p.trans = 0;
+        p.ctr = ctr; p.timeout = flag;
+        p.wait_ns = (long long)wait_ms * 1000000ll;
+        trsv_chain_kernel<<<1, kThreads>>>(p);
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(&h, flag, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(xh, x, sizeof xh, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(left, ctr, sizeof left, cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = GBQR_ECUDA;
+    }
+    cudaFree(d);
+    if (st != GBQR_OK) return st;
+    // blocks solved: the waiting block (rows 0..63) would have been overwritten
+    int solved = 0;
+    for (int i = 0; i < B; ++i) solved |= (xh[i] != 1.0) ? 1 : 0;
+    *completed = solved;
+    for (int i = 0; i < kNumCounters; ++i)
+        if (left[i] != 0u) return GBQR_ECUDA;   // the counters must be left zero for the next launch
+    return h ? GBQR_ETIMEOUT : GBQR_OK;
+}

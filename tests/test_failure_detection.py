@@ -3,7 +3,9 @@ tensor-core GEMM uses gives up after its time limit on a barrier nothing
 arrives at, raises the error flag and returns; the host reads GBQR_ETIMEOUT
 and the device keeps working (a mixed-precision factorization right after
 matches the oracle).  The same for the persistent batched kernel's bounded
-dependency wait, on a task whose dependency never completes."""
+dependency wait, on a task whose dependency never completes, and for the
+persistent triangular-solve chain, on a block whose predecessor is never
+solved."""
 
 import ctypes
 
@@ -48,4 +50,26 @@ def test_batched_dependency_wait_times_out_and_device_survives(gb, orc):
     assert st == gb.GBQR_OK
     for a, A, T in zip(mats, As, Ts):
         _gpu.compare_factor(a, gb.to_numpy(A), gb.to_numpy(T), gb.GBQR_T_PANEL, 16, orc, f"after timeout {a.shape}")
+    ctx.close()
+
+
+def test_chain_wait_times_out_and_device_survives(gb, orc):
+    """The persistent triangular-solve chain's bounded wait (the same wait
+    as the one-vector Q application's): a CTA handed a block whose
+    predecessor is never solved gives up, raises the timeout flag and
+    resets the launch counters; a mixed least-squares solve (both one-launch
+    kernels) then still matches the oracle."""
+    import torch
+    completed = ctypes.c_int(-2)
+    st = gb.gbqr_selftest_chain_wait(0, 300, ctypes.byref(completed))
+    assert st == gb.GBQR_ETIMEOUT and completed.value == 0
+    ctx = gb.Context(0)
+    a, _, b = workloads.ls_problem(1500, 200, 2.0, 61)
+    A = _gpu.device_matrix(a)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(200, dtype=torch.float64, device="cuda")
+    st, info = ctx.ls_solve(A, bd, x, gb.GBQR_MIXED_SPLITBF16)
+    assert st == gb.GBQR_OK
+    x_o, _ = orc.ls_solve(a, b)
+    assert np.linalg.norm(x.cpu().numpy() - x_o) / np.linalg.norm(x_o) <= max(1e-12, 50 * np.linalg.cond(a) * 2.0 ** -53)
     ctx.close()
