@@ -129,7 +129,12 @@ Layout make_layout(int64_t m, int64_t n, int t_layout, const Params &pr, int num
     Layout L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + std::max<size_t>(bytes, 16), 256); return o; };
-    L.n_partial = gemm_partial_elems_max(num_sms);
+    // split-K scratch grows with the problem (a quarter of m n elements per
+    // lane) between what 4 and 16 split CTAs per SM need: the planner splits
+    // only as far as the buffer allows
+    L.n_partial = std::min(gemm_partial_elems_max(num_sms),
+                           std::max(gemm_partial_elems_min(num_sms),
+                                    (size_t)std::max<int64_t>(m, 1) * (size_t)std::max<int64_t>(n, 1) / 4));
     L.n_gcount = gemm_counters_max(num_sms);
     const int w = (int)std::max<int64_t>(1, std::min<int64_t>(pr.b, n));
     L.tsqr = tsqr_plan_bound(std::max<int64_t>(m, 1), w, pr.leaf_rows, pr.fanout, num_sms);

@@ -73,7 +73,8 @@ struct GemmScratchT {
 };
 using GemmScratch = GemmScratchT<double>;
 
-size_t gemm_partial_elems_max(int num_sms);
+size_t gemm_partial_elems_max(int num_sms);   // the most split-K scratch the planner can use
+size_t gemm_partial_elems_min(int num_sms);   // enough for 4 split CTAs per SM
 size_t gemm_counters_max(int num_sms);
 // Real = double (FP64 path) or float (FP32 batched path)
 template <class Real>

@@ -364,16 +364,24 @@ cudaError_t launch_bm(int BN, const GemmParamsT<Real> &p, bool ta, dim3 grid, cu
     }
 }
 
-constexpr int kMaxSplitCtasPerSm = 4;
+// At most this many split CTAs per SM.  The split count also stops where the
+// partial tiles would not fit the caller's scratch, so a smaller buffer only
+// limits the splitting.  (A 128 x 7936 product of graded 8192^2 - 252 tiles
+// over K = 8192 - split 2 at 4 CTAs per SM left 48 SMs with 4 CTAs and 104
+// with 3, 1.06 TFLOP/s; split 3 or more, 1.20.)
+constexpr int kMaxSplitCtasPerSm = 16;
+constexpr int kBaseSplitCtasPerSm = 4;
+
+size_t partial_elems_for(int ctas_per_sm, int num_sms) {
+    // the reduction tree adds at most a quarter more slots, plus a few per tile
+    const size_t ctas = (size_t)ctas_per_sm * num_sms;
+    return (ctas + ctas / 4 + 64) * 64 * 64;
+}
 
 }  // namespace
 
-size_t gemm_partial_elems_max(int num_sms) {
-    // at most kMaxSplitCtasPerSm*num_sms CTAs take part in split launches;
-    // the reduction tree adds < 1/7 more slots plus a few per tile.
-    size_t ctas = (size_t)kMaxSplitCtasPerSm * num_sms;
-    return (ctas * 2 + 64) * 64 * 64;
-}
+size_t gemm_partial_elems_max(int num_sms) { return partial_elems_for(kMaxSplitCtasPerSm, num_sms); }
+size_t gemm_partial_elems_min(int num_sms) { return partial_elems_for(kBaseSplitCtasPerSm, num_sms); }
 
 size_t gemm_counters_max(int num_sms) { return (size_t)kMaxSplitCtasPerSm * num_sms * 2 + 64; }
 
@@ -427,6 +435,13 @@ gbqr_status gemm(const Exec &ex, const GemmOpT<Real> &op, const GemmScratchT<Rea
         const int64_t smax = std::min<int64_t>({ktiles / per, (int64_t)kMaxSplitCtasPerSm * ex.num_sms / tiles, 512});
         double best = -1.0;
         for (int64_t s = 1; s <= smax; ++s) {
+            if (s > 1) {   // the split's partial tiles and counters must fit the scratch
+                int sl = 1, ct = 1;
+                tree_shape((int)s, &sl, &ct);
+                if (!sc.partial || !sc.counters || (size_t)tiles * sl * BM * BN > sc.partial_elems ||
+                    (size_t)tiles * ct > sc.ncounters)
+                    continue;
+            }
             const double ctas = (double)(tiles * s);
             const double waves = std::ceil(ctas / ex.num_sms);
             // useful fraction of the occupied SM-waves, lightly favouring more parallelism
