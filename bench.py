@@ -60,8 +60,8 @@ FP64_PEAK_TFLOPS = SM_COUNT * FP64_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
 # configuration.
 DGEMM_TRAFFIC_RATIO = {
     # (workload, panel_nb, cutoff_b, engine): ratio
-    ("graded_8192x8192", 128, 16, "dfma"): 0.764,
-    ("graded_4096x4096", 128, 16, "dfma"): 0.764,
+    ("graded_8192x8192", 128, 16, "dfma"): 0.780,
+    ("graded_4096x4096", 128, 16, "dfma"): 0.780,
 }
 DGEMM_TRAFFIC_SOURCE = "ncu: all dgemm launches of graded 4096x4096 (nb 128, b 16, DFMA), dram read+write / algorithmic"
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs peak; LS solves/s, p99 ms: mixed vs FP64"
