@@ -81,7 +81,7 @@ typedef enum {
     GBQR_MIXED_BF16 = 1,    /* reserved: tensor-core update GEMMs + refinement */
     GBQR_MIXED_SPLITBF16 = 2,
     GBQR_FP32 = 3,
-    GBQR_PREC_AUTO = 4      /* serving: mixed for large problems (n >= 256, m n^2 >= 4e9),
+    GBQR_PREC_AUTO = 4      /* serving: mixed for large problems (n >= 256, m n^2 >= 1e9),
                                FP64 otherwise, FP64 again when refinement fails */
 } gbqr_prec;
 

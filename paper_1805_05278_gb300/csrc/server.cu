@@ -50,12 +50,14 @@ struct Record {
 
 // GBQR_PREC_AUTO: the tensor-core updates only pay off where the update
 // GEMMs dominate the solve.  Measured single-solve speed-ups of the mixed
-// path over FP64 (graded columns, kappa ~ 1e4): 2.71x at 65536 x 1024, 1.76x
-// at 65536 x 512, 1.24x at 16384 x 512, 1.23x at 65536 x 256, 1.05x at
-// 4096 x 1024 (all m n^2 >= 4e9), 1.04x at 16384 x 256, slower below (the
-// FP64 panel chain dominates and the refinement adds its GMRES steps).
+// path over FP64 (graded columns, kappa ~ 1e4, two GMRES steps each):
+// 3.19x at 65536 x 1024, 1.96x at 65536 x 512, 1.88x at 16384 x 1024,
+// 1.36x at 16384 x 512, 1.32x at 65536 x 256, 1.12x at 8192 x 512, 1.08x
+// at 16384 x 256, 1.01x at 2048 x 1024 (all m n^2 >= 1e9); slower below
+// (0.96x at 8192 x 256, 0.93x at 2048 x 512) and at n <= 128 (0.63-0.94x):
+// there the FP64 panel chain dominates and the refinement adds its steps.
 int auto_precision(int64_t m, int64_t n) {
-    return (n >= 256 && (double)m * n * n >= 4e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
+    return (n >= 256 && (double)m * n * n >= 1e9) ? GBQR_MIXED_SPLITBF16 : GBQR_FP64;
 }
 
 // The request's own device operands: A (lda x n), b (m) and x (n), FP64.
