@@ -75,10 +75,15 @@ def test_apply_and_form_q(gb, ctx, orc, m, n, seed, layout_name):
     (3000, 200, 64, "panel"),     # narrower boxes, deeper ring
     (1024, 128, 128, "panel"),    # one panel, one chunk per item: the item's last chunk in ring slot 0
     (16384, 128, 128, "panel"),   # four chunks per item in a three-slot ring
+    (1000, 77, 0, "full"),        # full T with an odd panel width: T read from global memory
+    (33, 32, 32, "panel"),        # one row past a chunk
+    (129, 128, 64, "panel"),      # two panels, the second one row taller than its triangle
 ])
 def test_apply_one_vector(gb, ctx, orc, m, n, nb, layout_name):
-    """Q^T b and Q b of a single vector (the one-launch-per-panel path) against
-    the oracle, for both directions, ragged panels and multi-level trees."""
+    """Q^T b and Q b of a single vector (one persistent launch per
+    application) against the oracle, for both directions, ragged panels,
+    multi-group share trees, the tensor-box and per-lane-load row paths and
+    T staged in shared memory or read from global memory."""
     import torch
     layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
     nb = nb if layout == gb.GBQR_T_PANEL else n
