@@ -56,7 +56,7 @@ static_assert(kTmaMaxW <= 32 * (kWarps - 1), "the warp staging T is not one of t
 enum { kTicket = 0, kArrive = 1, kReady = 2, kDone = 3, kAbort = 4, kGroupCtr = 5, kNumCounters = kGroupCtr + kMaxGroups };
 
 struct ApplyVec {
-    int64_t m, lda, ldt, R;    // R: rows per item (a multiple of kChunkL)
+    int64_t m, lda, ldt, R;    // R: rows per item (a multiple of kChunkT on the TMA path, else of kChunkL)
     int n, pb, npan, nblk;     // panel width, panels, row blocks
     int trans, tfull;          // Q^T (else Q); T is the full n x n kernel (else nb x n panel kernels)
     int tsm, stages, tstride;  // T staged by bulk copies; TMA ring depth; staged T's column stride
@@ -156,14 +156,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
 }
 
 // Wait for the mbarrier phase of the given parity (every thread of the CTA
-// calls it).  Bounded: gives up after the launch's wait limit, or as soon as
-// another CTA has raised the abort flag, and then raises the flags itself.
-__device__ bool mbar_wait(const ApplyVec &p, uint32_t a, uint32_t parity) {
+// calls it).  Bounded: gives up after the launch's wait limit, and then
+// raises the flags.  With stop_on_abort it also gives up as soon as another
+// CTA has raised the abort flag; waits for this CTA's own copies in flight
+// (before it reuses or leaves its shared memory) pass false.
+__device__ bool mbar_wait(const ApplyVec &p, uint32_t a, uint32_t parity, bool stop_on_abort = true) {
     if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
         if (mbar_try(a, parity)) return true;
-        if (*(volatile unsigned *)(p.ctr + kAbort)) return false;
+        if (stop_on_abort && *(volatile unsigned *)(p.ctr + kAbort)) return false;
         if (global_ns() - t0 > (unsigned long long)p.wait_ns) {
             atomicExch(p.ctr + kAbort, 1u);
             atomicExch(p.timeout, 1);
@@ -333,7 +335,7 @@ __device__ __forceinline__ void ring_issue(const CUtensorMap *map, const ApplyVe
 __device__ void ring_drain(const ApplyVec &p, Smem &sm, Ring &rg) {
     while (rg.used < rg.issued) {
         const int slot = rg.used % p.stages;
-        mbar_wait(p, smem_u32(&sm.full[slot]), (rg.ph >> slot) & 1u);
+        mbar_wait(p, smem_u32(&sm.full[slot]), (rg.ph >> slot) & 1u, false);
         rg.ph ^= 1u << slot;
         ++rg.used;
     }
@@ -371,7 +373,11 @@ __device__ bool item_rows_tma(const CUtensorMap *map, const ApplyVec &p, const S
             }
             sm.part[g * 32 + lane] = a;
         }
-        if (__syncthreads_or(!ok)) return false;         // a wait ran out: the whole CTA stops
+        if (__syncthreads_or(!ok)) {                     // a wait ran out: the whole CTA stops,
+            rg.ph ^= 1u << slot;                         // and this chunk counts as still in
+            --rg.used;                                   // flight for the caller's drain
+            return false;
+        }
         // the slot of chunk i - 1 is free: every warp finished it before this
         // barrier (all threads count the issue, thread 0 makes it)
         if (i >= 1 && rg.issued < rg.nch) {
@@ -515,7 +521,7 @@ __device__ void arrive_item(const ApplyVec &p, const Stage &st, Smem &sm, int s,
     }
     double *y = p.y + (s & 1) * p.pb;
     if (staged) {
-        const bool ok = __syncthreads_and(mbar_wait(p, smem_u32(&sm.tbar), sm.tpar));
+        const bool ok = __syncthreads_and(mbar_wait(p, smem_u32(&sm.tbar), sm.tpar, false));
         if (ok) t_product<true>(p, st, sm, Ts, p.tstride, y);   // else the launch is aborting
         __syncthreads();
         if (tid == 0) sm.tpar ^= 1u;
