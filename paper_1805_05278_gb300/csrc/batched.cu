@@ -218,7 +218,7 @@ __device__ __forceinline__ void v_rows(const Real *S, int ldS, int r0, int h, co
 // Panel task (flat-tree TSQR in one CTA, then the Householder
 // reconstruction); returns non-zero if the panel held a NaN or Inf.
 // Shared memory: S (ldS x b), then Tt, G, Mx, Bm, Cm, X, Li, Ui (b x b each,
-// used with leading dimension w), then 7 b reflector scalars and signs.
+// used with leading dimension w), then 8 b reflector scalars and signs.
 template <int MaxB, class Real>
 __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Real *sm, Real *tscr) {
     const int b = p.b, tid = threadIdx.x, nthr = blockDim.x;
@@ -232,7 +232,7 @@ __device__ int panel_task(const BParams<Real> &p, const BMat<Real> &M, int k, Re
     Real *Tt = S + (size_t)ldS * b;
     Real *G = Tt + bb, *Mx = G + bb, *Bm = Mx + bb, *Cm = Bm + bb, *X = Cm + bb, *Li = X + bb, *Ui = Li + bb;
     Real *aux = Ui + bb;
-    const Refl<Real> rf{aux, aux + w, aux + 2 * w, aux + 3 * w, aux + 4 * w};
+    const Refl<Real> rf{aux, aux + w, aux + 2 * w, aux + 3 * w, aux + 4 * w, aux + 7 * b};
     Real *Sg = aux + 5 * b, *rU = Sg + b;
     const int P = (mr + p.hblk - 1) / p.hblk;
     auto rb = [&](int q) { return (int)((int64_t)q * mr / P); };
@@ -595,7 +595,7 @@ const void *kernel_for(int b) {
 }
 
 size_t panel_smem(int b, int hblk, size_t real) {
-    return real * ((size_t)(hblk + b) * b + 8 * (size_t)b * b + 7 * (size_t)b);
+    return real * ((size_t)(hblk + b) * b + 8 * (size_t)b * b + 8 * (size_t)b);
 }
 size_t update_smem(int b, int hup, size_t real) {
     return real * (2 * (size_t)(hup + 1) * (b + kUpdCols) + (size_t)b * kUpdCols + (size_t)b * b);

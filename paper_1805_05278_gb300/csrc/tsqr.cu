@@ -74,7 +74,7 @@ __device__ __forceinline__ void load_stack(Real *S, int64_t ldS, const Real *src
 __device__ __forceinline__ int64_t leaf_begin(int64_t mp, int P, int p) { return (int64_t)p * mp / P; }
 
 // Up kernel shared memory: S (ldS x w), then T, G (w x w each), then the
-// per-column reflector data (Refl: tau, d, beta*d, q, 1/d; w each).
+// per-column reflector data (Refl: tau, d, beta*d, q, 1/d, norm; w each).
 template <class Real>
 __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_up_kernel(TsqrParamsT<Real> p) 
     Real *T = S + (size_t)ldS * w;
     Real *G = T + w * w;
     Real *aux = G + w * w;
-    const Refl<Real> rf{aux, aux + w, aux + 2 * w, aux + 3 * w, aux + 4 * w};
+    const Refl<Real> rf{aux, aux + w, aux + 2 * w, aux + 3 * w, aux + 4 * w, aux + 5 * w};
     __shared__ int s_last;
 
     const int leaf = blockIdx.x;
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) tsqr_down_kernel(TsqrParamsT<Real> p
     }
 }
 
-size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + 5 * (size_t)w); }
+size_t up_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 2 * (size_t)w * w + 6 * (size_t)w); }
 size_t down_smem(int ldS, int w) { return sizeof(double) * ((size_t)ldS * w + 5 * (size_t)w * w + 2 * w); }
 
 constexpr size_t kSmemCap = 200 * 1024;
@@ -395,7 +395,7 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     pl.mp = mp; pl.w = w;
     // tallest leaf that every kernel's shared memory can hold
     const size_t cap_el = kSmemCap / sizeof(double);
-    int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + 5 * (size_t)w)) / w);          // up
+    int64_t hcap = (int64_t)((cap_el - (2 * (size_t)w * w + 6 * (size_t)w)) / w);          // up
     hcap = std::min<int64_t>(hcap, (int64_t)((cap_el - 5 * (size_t)w * w - 2 * w) / w));   // down + recon
     if (hcap < w) return false;
     // default: about one leaf per SM (the leaf phase is the only one that

@@ -87,6 +87,7 @@ __device__ __forceinline__ void load_block(Real *dst, int64_t ldd, const Real *s
 // Rows of column j below its pivot in a leaf block: j+1 .. h-1.
 struct LeafRows {
     int h;
+    static constexpr bool kNextPivotInB = true;   // step j touches row j+1
     template <class F>
     __device__ __forceinline__ void each(int j, int lane, F &&f) const {
         for (int r = j + 1 + lane; r < h; r += 32) f(r);
@@ -112,6 +113,7 @@ struct LeafRows {
 // by (q, s) with at most one carry and only the first entry needs a division.
 struct MergeRows {
     int w, cnt;
+    static constexpr bool kNextPivotInB = false;
     // Of the rows step j touches, those below the pivot of column j+1 (every
     // triangle after the first); row j+1 of those triangles is below that
     // pivot too but outside step j's rows.
@@ -151,6 +153,7 @@ struct MergeRows {
 // Householder vectors are [e_j; y_j] and V = [I; Y].
 struct StackRows {
     int w, h;
+    static constexpr bool kNextPivotInB = false;
     template <class F>
     __device__ __forceinline__ void each(int, int lane, F &&f) const {
         for (int r = w + lane; r < w + h; r += 32) f(r);
@@ -170,11 +173,12 @@ struct StackRows {
 // cancellation) and x the column below its pivot, the normalised vector is
 // v = [1; x/d] and tau = (beta - alpha)/beta; with vh = [d; x] and
 // q = 1/(beta d) the same reflector is H = I - tau v v^T = I + q vh vh^T.
-// So the pivot warp only publishes beta (on the pivot), d and beta*d: the
-// reciprocal q is taken by the next step's pivot warp, overlapped with its
-// dot products, and the scaling of x by 1/d, tau and the Gram entries are
-// settled once per block (finish_block).  A zero column (beta = 0) is stored
-// as d = 1, beta*d = 0, and q_of maps it to q = -2: H = I - 2 e e^T, tau = 2.
+// So the pivot warp only publishes beta (on the pivot), d, beta*d and the
+// squared norm below the pivot: the reciprocal q is taken by another warp
+// during the next step, and the scaling of x by 1/d, tau and the Gram entries
+// are settled once per block (finish_block).  A zero column (beta = 0) is
+// stored as d = 1, beta*d = 0, and q_of maps it to q = -2: H = I - 2 e e^T,
+// tau = 2.
 template <class Real>
 struct Refl {
     Real *tau;   // tau[c], from finish_block on
@@ -182,39 +186,49 @@ struct Refl {
     Real *bd;    // beta[c] * d[c]  (0 for a zero column)
     Real *q;     // q[c] = 1/(beta d), published in step c
     Real *sc;    // 1/d[c], from finish_block on
+    Real *sg;    // squared norm of column c below its pivot, published with it
 };
 
 template <class Real>
 __device__ __forceinline__ Real q_of(Real bd) { return bd == Real(0) ? Real(-2) : real_rcp(bd); }
 
-// Named barrier 1 hands q_j from the pivot warp (bar.arrive) to the six warps
-// that update other columns (bar.sync): 7 warps, 224 threads.  Every step the
-// pivot warp arrives exactly once and each of those six warps syncs exactly
-// once; the eighth warp (the pivot warp's sub-partition partner) takes no part.
+// q_j goes from the warp that computes it (the pivot warp's sub-partition
+// partner, bar.arrive on both) to the six warps that update other columns
+// through named barrier 1 (7 warps) and to the pivot warp through named
+// barrier 2 (2 warps), so that neither waits for the other.  Every step the
+// partner arrives once at each, and each of the other seven warps syncs
+// exactly once at its own.
 constexpr int kQBarrier = 1;
 constexpr int kQThreads = 7 * 32;
+constexpr int kQPivotBarrier = 2;
+constexpr int kQPivotThreads = 2 * 32;
 // (barrier.* without .aligned: correct even where a warp is not converged)
 __device__ __forceinline__ void q_arrive() {
     __syncwarp();
     asm volatile("barrier.arrive %0, %1;" ::"n"(kQBarrier), "n"(kQThreads) : "memory");
+    asm volatile("barrier.arrive %0, %1;" ::"n"(kQPivotBarrier), "n"(kQPivotThreads) : "memory");
 }
 __device__ __forceinline__ void q_sync() {
     __syncwarp();
     asm volatile("barrier.sync %0, %1;" ::"n"(kQBarrier), "n"(kQThreads) : "memory");
 }
+__device__ __forceinline__ void q_sync_pivot() {
+    __syncwarp();
+    asm volatile("barrier.sync %0, %1;" ::"n"(kQPivotBarrier), "n"(kQPivotThreads) : "memory");
+}
 
-// One warp turns column c (squared norm below its pivot sig2) into an
-// unnormalised reflector: beta on the pivot, d and beta*d published.
+// One warp turns column c (pivot entry alpha, squared norm below the pivot
+// sig2) into an unnormalised reflector: beta on the pivot; d, beta*d and
+// sig2 published.
 template <class Real>
-__device__ __forceinline__ void publish_pivot(Real *S, int ldS, int c, const Refl<Real> &rf, Real sig2) {
+__device__ __forceinline__ void publish_pivot(Real *S, int ldS, int c, const Refl<Real> &rf, Real alpha, Real sig2) {
     const int lane = threadIdx.x & 31;
     Real *col = S + (size_t)c * ldS;
-    const Real alpha = col[c];
     const Real nrm = real_sqrt(rfma(alpha, alpha, sig2));
     const Real beta = alpha < Real(0) ? nrm : -nrm;
     const Real d = beta != Real(0) ? alpha - beta : Real(1);
     __syncwarp();
-    if (lane == 0) { col[c] = beta; rf.d[c] = d; rf.bd[c] = beta * d; }
+    if (lane == 0) { col[c] = beta; rf.d[c] = d; rf.bd[c] = beta * d; rf.sg[c] = sig2; }
     __syncwarp();
 }
 
@@ -224,46 +238,70 @@ __device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, const Refl
     const Real *col = S + (size_t)c * ldS;
     Real part = Real(0);
     rows.each(c, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
-    publish_pivot(S, ldS, c, rf, warp_sum(part));
+    publish_pivot(S, ldS, c, rf, col[c], warp_sum(part));
 }
 
-// The pivot warp's share of step j: q_j for the other warps (named barrier),
-// then reflector j applied to column c = j+1 with the squared norm of column c
-// below its pivot summed in the same pass, then column c published.
+// The pivot warp's share of step j: reflector j applied to column c = j+1,
+// then column c published as the next reflector.  With x = column c before
+// the step, v = vh_j and f = q_j vh_j^T x, the rows B below pivot j are
+// updated to x + f v, so the squared norm of column c below its own pivot is
+//     S2 + f (2 S3 + f s4)   (minus the new pivot entry's square where B
+//                             holds it, as in a leaf block),
+// with S2 = sum of x^2 over B and over the rows below pivot c outside B,
+// S3 = sum of v x over B and s4 = sum of v^2 over B, which is column j's
+// published norm.  So one
+// pass over the rows and one warp reduction (of S2 and S3) come before the
+// square root, instead of a pass, a reduction, a second pass and a second
+// reduction.  Where the three terms cancel (the result is below half their
+// magnitude, so it would carry more than a few rounding errors of them),
+// the norm is summed directly from the updated rows instead.
 template <class Real, class Rows>
 __device__ void pivot_step(Real *S, int ldS, int j, int w, const Rows &rows, const Refl<Real> &rf) {
     const int lane = threadIdx.x & 31, c = j + 1;
+    if (c >= w) { q_sync_pivot(); return; }        // last step: q_j is only stored
     const Real dj = rf.d[j];
     const Real *vj = S + (size_t)j * ldS;
     Real *col = S + (size_t)c * ldS;
-    Real acc = Real(0);
-    if (c < w) rows.each_with_pivot(j, lane, [&](int r, bool piv) { acc = rfma(piv ? dj : vj[r], col[r], acc); });
-    // the reciprocal and the reduction are independent chains: nothing
-    // between them, so their latencies overlap
-    const Real qj = q_of(rf.bd[j]);
-    acc = warp_sum(acc);
-    if (lane == 0) rf.q[j] = qj;
-    __syncwarp();
-    __threadfence_block();
-    q_arrive();
-    if (c >= w) return;
-    const Real f = qj * acc;
-    Real part = Real(0);
-    rows.each_with_pivot(j, lane, [&](int r, bool piv) {
-        const Real x = rfma(f, piv ? dj : vj[r], col[r]);
-        col[r] = x;
-        if (rows.below_next(j, r)) part = rfma(x, x, part);
+    const Real xj = col[j];                        // row j of column c, before the step
+    const Real xc = col[c], vc = vj[c];            // the next pivot row
+    Real s3 = Real(0), s2 = Real(0);
+    rows.each(j, lane, [&](int r) {
+        const Real x = col[r];
+        s3 = rfma(vj[r], x, s3);
+        s2 = rfma(x, x, s2);
     });
-    rows.each_untouched(j, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
-    const Real sig2 = warp_sum(part);
-    __syncwarp();
-    publish_pivot(S, ldS, c, rf, sig2);
+    rows.each_untouched(j, lane, [&](int r) { const Real x = col[r]; s2 = rfma(x, x, s2); });
+    Real sums[4] = {s3, s2, Real(0), Real(0)};
+    warp_sum_n<2>(sums);
+    const Real S3 = sums[0], S2 = sums[1], s4 = rf.sg[j];
+    q_sync_pivot();                                // q_j from the partner warp
+    const Real f = rf.q[j] * rfma(dj, xj, S3);
+    const Real sumB = rfma(f, rfma(f, s4, Real(2) * S3), S2);
+    Real alpha = xc, sig2 = sumB;
+    if (Rows::kNextPivotInB) {
+        alpha = rfma(f, vc, xc);
+        sig2 = rfma(-alpha, alpha, sumB);
+    }
+    const bool direct = !(sig2 >= Real(0.5) * rfma(f * f, s4, S2));
+    if (!direct) {
+        rows.each_with_pivot(j, lane, [&](int r, bool piv) { col[r] = rfma(f, piv ? dj : vj[r], col[r]); });
+    } else {
+        Real part = Real(0);
+        rows.each_with_pivot(j, lane, [&](int r, bool piv) {
+            const Real x = rfma(f, piv ? dj : vj[r], col[r]);
+            col[r] = x;
+            if (rows.below_next(j, r)) part = rfma(x, x, part);
+        });
+        rows.each_untouched(j, lane, [&](int r) { const Real x = col[r]; part = rfma(x, x, part); });
+        sig2 = warp_sum(part);
+    }
+    publish_pivot(S, ldS, c, rf, alpha, sig2);
 }
 
 // One warp applies reflector j to N columns (c > j: A(:,c) += q_j vh_j
 // (vh_j^T A(:,c))) or, for c < j, records the unscaled Gram entry
 // vh_c^T vh_j (scaled to v_c^T v_j by finish_block).  q_j is taken from the
-// pivot warp through the named barrier, once per step (*synced).
+// partner warp through the named barrier, once per step (*synced).
 template <int N, class Real, class Rows>
 __device__ __forceinline__ void warp_apply(Real *S, int ldS, int j, const Rows &rows, const int (&cols)[4],
                                            const Refl<Real> &rf, Real *G, int w, bool *synced, Real *qj) {
@@ -299,12 +337,14 @@ __device__ __forceinline__ void warp_apply(Real *S, int ldS, int j, const Rows &
 // it into the next reflector while six others share every remaining column
 // round robin, so each step needs one CTA barrier (and the q_j hand-over).
 // On GB300 a warp issues at most one FP64 instruction per ~64 cycles and an
-// SM sub-partition one per ~76, so the step time is the FP64 instruction
-// count of the busiest warp / sub-partition: the pivot warp (square root,
-// two warp reductions) carries nothing else, and the warp that shares its
-// sub-partition (warp i runs on sub-partition i % 4) gets no columns.
-// Leaves the reflectors unnormalised (vh_c below the pivots, d, beta*d, q);
-// finish_block settles them.
+// SM sub-partition one per ~76, and a dependent FP64 result takes ~125
+// cycles, so the step time is the longer of the pivot warp's dependency
+// chain and the FP64 instruction count of the busiest sub-partition: the
+// pivot warp (square root, one warp reduction) carries nothing else, and the
+// warp that shares its sub-partition (warp i runs on sub-partition i % 4)
+// only takes the reciprocal q_j off the pivot warp's chain.  Leaves the
+// reflectors unnormalised (vh_c below the pivots, d, beta*d, q); finish_block
+// settles them.
 template <class Real, class Rows>
 __device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, const Refl<Real> &rf, Real *G) {
     static_assert(kThreads == 256, "the q_j hand-over is laid out for 8 warps");
@@ -318,7 +358,12 @@ __device__ void householder_block(Real *S, int ldS, int w, const Rows &rows, con
         const int partner = (pw + 4) % nw;
         if (wid == pw) {
             pivot_step(S, ldS, j, w, rows, rf);
-        } else if (wid != partner) {
+        } else if (wid == partner) {
+            if ((threadIdx.x & 31) == 0) rf.q[j] = q_of(rf.bd[j]);
+            __syncwarp();
+            __threadfence_block();
+            q_arrive();
+        } else {
             const int nexcl = (nxt < w) ? 2 : 1;
             const int ncols = w - nexcl;
             constexpr int nwork = nw - 2;

@@ -102,6 +102,30 @@ def test_upper_triangular_input(gb, ctx, orc):
     _gpu.compare_factor(a, VR, T, gb.GBQR_T_FULL, nb, orc, "upper triangular")
 
 
+def _near_pairs(m, n, seed, eps=1e-3):
+    """Odd columns nearly parallel to the even column before them: after the
+    reflector of column 2k, column 2k+1 keeps about eps of its norm, so the
+    norm below its pivot cancels in every leaf, merge and stacked block."""
+    a = workloads.gaussian(m, n, seed)
+    a[:, 1::2] = a[:, 0:n - n % 2:2] + eps * a[:, 1::2]
+    return a
+
+
+@pytest.mark.parametrize("layout_name", ["full", "panel"])
+@pytest.mark.parametrize("leaf,k", [(0, 0), (64, 4), (40, 2)])
+def test_nearly_parallel_columns(gb, ctx, orc, layout_name, leaf, k):
+    """The pivot step takes the norm of the updated column from sums of the
+    column before the update; where those terms cancel it sums the updated
+    rows instead.  Columns chosen to cancel at every tree level still match
+    the oracle element by element (a norm kept from the cancelling terms
+    would put errors near 1e-9 into V and T)."""
+    layout = gb.GBQR_T_FULL if layout_name == "full" else gb.GBQR_T_PANEL
+    a = _near_pairs(2000, 40, 17)
+    o = gb.opts(cutoff_b=16, leaf_rows=leaf, fanout=k)
+    VR, T, nb = _gpu.factor_gpu(ctx, a, layout, o)
+    _gpu.compare_factor(a, VR, T, layout, nb, orc, f"near pairs leaf={leaf} k={k} {layout_name}")
+
+
 def test_zero_column_gives_a_valid_qr(gb, ctx):
     """Rank deficiency: V, T are not unique, so check A = QR and Q^T Q = I."""
     import torch
