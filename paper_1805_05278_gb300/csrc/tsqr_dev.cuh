@@ -249,10 +249,9 @@ __device__ void warp_pivot(Real *S, int ldS, int c, const Rows &rows, const Refl
 //                             holds it, as in a leaf block),
 // with S2 = sum of x^2 over B and over the rows below pivot c outside B,
 // S3 = sum of v x over B and s4 = sum of v^2 over B, which is column j's
-// published norm.  So one
-// pass over the rows and one warp reduction (of S2 and S3) come before the
-// square root, instead of a pass, a reduction, a second pass and a second
-// reduction.  Where the three terms cancel (the result is below half their
+// published norm.  So one pass over the rows and one warp reduction (of S2
+// and S3) come before the square root, instead of a pass, a reduction, a
+// second pass and a second reduction.  Where the three terms cancel (the result is below half their
 // magnitude, so it would carry more than a few rounding errors of them),
 // the norm is summed directly from the updated rows instead.
 template <class Real, class Rows>
