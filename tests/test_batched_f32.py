@@ -116,3 +116,22 @@ def test_f32_single_factorization(gb, orc, m, n, layout_name, nb):
     _gpu.compare_factor(a.astype(np.float64), A.cpu().numpy(), T.cpu().numpy(), layout, nbr, orc,
                         f"fp32 {m}x{n}", fp32=True)
     ctx.close()
+
+
+@pytest.mark.parametrize("leaf,k", [(0, 0), (40, 2)])
+def test_f32_nearly_parallel_columns(gb, orc, leaf, k):
+    """The pivot step's direct-sum branch in FP32: odd columns 3e-3 away from
+    the even ones, so after each reflector the next column's norm cancels in
+    every leaf and merge.  Against the FP64 oracle on the same float32 input
+    (a norm kept from the cancelling sums would be off by ~1e-1 here)."""
+    import torch
+    from tests.test_parity_factor import _near_pairs
+    a = _near_pairs(2000, 40, 23, 3e-3).astype(np.float32)
+    ctx = gb.Context(0)
+    A = _device32(a)
+    T = torch.full((40, 40), float("nan"), dtype=torch.float32, device="cuda").T
+    ctx.factor(A, T, gb.GBQR_T_FULL, gb.opts(cutoff_b=16, leaf_rows=leaf, fanout=k))
+    torch.cuda.synchronize()
+    _gpu.compare_factor(a.astype(np.float64), A.cpu().numpy(), T.cpu().numpy(), gb.GBQR_T_FULL, 40, orc,
+                        f"fp32 near pairs leaf={leaf} k={k}", fp32=True)
+    ctx.close()
