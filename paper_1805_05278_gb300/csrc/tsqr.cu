@@ -404,6 +404,10 @@ bool tsqr_plan(int64_t mp, int w, int leaf_rows, int fanout, int num_sms, TsqrPl
     // never shorter than the panel is wide
     const int sms = num_sms > 0 ? num_sms : 152;
     int64_t target = leaf_rows > 0 ? leaf_rows : std::max<int64_t>({(int64_t)w, (int64_t)128, (mp + sms - 1) / sms});
+    // ... and up to 256 rows where that saves a whole merge level (17 to 32
+    // leaves of 128 rows become 16 of at most 256: one merge instead of two)
+    if (leaf_rows <= 0 && target == 128 && (mp + 127) / 128 > kMaxFanout && (mp + kMaxFanout - 1) / kMaxFanout <= 256)
+        target = (mp + kMaxFanout - 1) / kMaxFanout;
     target = std::max<int64_t>(target, w);
     int64_t P = (mp + target - 1) / target;
     P = std::max<int64_t>(P, (mp + hcap - 1) / hcap);   // leaves no taller than hcap
