@@ -94,7 +94,9 @@ typedef struct {
     int32_t cutoff_b;   /* QR-EG base-case threshold b: base case when n <= b
                            (Algorithm 2); 1 <= b <= 64 */
     int32_t panel_nb;   /* GBQR_T_PANEL: top-level panel width nb (>= 1) */
-    int32_t leaf_rows;  /* TSQR leaf height target m_p (>= b; Section 5 needs m_p >= n) */
+    int32_t leaf_rows;  /* TSQR leaf height target m_p (>= b; Section 5 needs m_p >= n);
+                           0 = about one leaf per SM, at least 128 rows, and up to
+                           256 where that leaves one merge level instead of two */
     int32_t fanout;     /* TSQR reduction-tree fan-out k (2..16; the paper's
                            binomial tree is k = 2, Appendix C.1; 0 = the
                            fewest merge levels with k <= 16, k >= 8) */
